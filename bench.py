@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark: Gbit/s scanned (Eq. 1: 8 * N / time) by the GB300 multi-pattern scan.
+
+Default workload: 256 MiB of seeded synthetic syslog text (2 % of lines carry a
+planted pattern) against 1,000 patterns of 4..64 bytes, 10 % of them
+prefixes of others.  A step is one full scan of the buffer -- every offset
+walked, every match written sorted to device memory, count included.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One JSON line on stdout (rank 0).  Under torchrun each rank scans its own copy
+of the workload (independent shards, no collective): weak scaling.
+``--impl reference`` times the CPU oracle (multi-threaded Aho-Corasick) on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TILE = 4096
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_workload(name: str):
+    import workloads as W
+    if name == "syslog-256MiB-1000pat":
+        return W.config2()
+    if name == "syslog-1MiB-100pat":
+        return W.config1()
+    if name == "dpi-2GiB-20000sig":
+        return W.config3()
+    if name == "files-10000-5000pat":
+        return W.config4()
+    if name.startswith("syslog-") and name.endswith("MiB-1000pat"):
+        return W.config2(int(name.split("-")[1][:-3]) * W.MiB)
+    raise SystemExit("unknown workload " + name)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the GPU works."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        time.sleep(0.05)
+        return self.summary()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    """The CPU oracle on this host's cores, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    w = make_workload(args.workload)
+    sample = w.text[: min(w.nbytes, args.ref_sample_mib * (1 << 20))]
+    cores = os.cpu_count() or 1
+    pats = w.patterns.csr()
+    for _ in range(args.warmup):
+        oracle.ac_mt(sample, pats, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.ac_mt(sample, pats, threads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    gbps = 8.0 * sample.size * len(times) / tot / 1e9
+    line = {
+        "impl": "reference", "metric": "Gbit/s scanned (8*N/t, Eq. 1)", "value": round(gbps, 4),
+        "unit": "Gbit/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * tot / len(times), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_bytes": int(sample.size)},
+        "cpu_baseline": {"value": round(gbps, 4), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+                         "sample": "first %d MiB of the workload, multi-threaded Aho-Corasick oracle, %d steps"
+                                   % (sample.size >> 20, args.steps)},
+        "e2e": {"value": round(gbps, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, budget_s: float = 20.0):
+    """The oracle as it stands on all host cores over a bounded sample of the workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    pats = w.patterns.csr()
+    n = min(w.nbytes, 64 << 20)
+    sample = w.text[:n]
+    t0 = time.perf_counter()
+    oracle.ac_mt(sample, pats, threads=cores)
+    dt = time.perf_counter() - t0
+    reps = 1
+    while dt * (reps + 1) / reps < budget_s / 4 and reps < 8 and n == w.nbytes:
+        t1 = time.perf_counter()
+        oracle.ac_mt(sample, pats, threads=cores)
+        dt += time.perf_counter() - t1
+        reps += 1
+    return {"value": round(8.0 * n * reps / dt / 1e9, 4), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d MiB of the workload x %d run(s), multi-threaded Aho-Corasick oracle" % (n >> 20, reps)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="syslog-256MiB-1000pat")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-sample-mib", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1704_02278_gb300 as glop
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    w = make_workload(args.workload)
+    N = w.nbytes
+    host = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+    host.numpy()[:] = w.text
+    text = host.to(dev)
+    seg = None
+    if w.seg is not None:
+        seg = torch.from_numpy(w.seg.view(np.int64).copy()).to(dev)
+    a = glop.Automaton(w.patterns)
+    stream = torch.cuda.Stream(device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    # size the output once (the count does not change between steps)
+    if seg is None:
+        m0, M = a.scan(text, stream=stream)
+    else:
+        m0, M = a.scan_batch(text, seg, stream=stream)
+    rec = 2 if seg is None else 3
+    matches = torch.empty((max(M, 1), rec), dtype=torch.int32, device=dev)
+    del m0
+    ws_buf = a.workspace(N, dev, None if seg is None else w.seg.size - 1)
+
+    def step():
+        if seg is None:
+            a.scan_into(text, matches, count, workspace=ws_buf, stream=stream)
+        else:
+            a.scan_batch_into(text, seg, matches, count, workspace=ws_buf, stream=stream)
+
+    clocks = ClockSampler(local).start()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(args.steps):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    total_ms = t_all0.elapsed_time(t_all1)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    st = a.status(dev, stream=stream, batch=seg is not None)
+    assert st == glop.OK, "scan status %s" % glop.STATUS.get(st)
+    assert int(count.item()) == M
+
+    t_max = total_ms
+    if pg:
+        tt = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+    gbps = 8.0 * N * args.steps * ws / (t_max / 1e3) / 1e9
+
+    # roofline of the scan (init + scan kernel per launch; the init kernel clears ~N/4096 words)
+    hbm, which = peaks()
+    halo = a.info["max_pattern_len"]
+    n_tiles = (N + TILE - 1) // TILE
+    algo_bytes = N + n_tiles * min(max(halo - 1, 16), 1024) + rec * 4 * M + 8 * n_tiles
+    avg_launch_ms = statistics.mean(per)
+    achieved = algo_bytes / (avg_launch_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned text in, matches out)
+    e2e = None
+    if seg is None and args.e2e_steps > 0:
+        hm = np.empty((M, 2), dtype=np.uint32)
+        staging = None
+        need = a.workspace_bytes(N)
+        import ctypes
+        sz = ctypes.c_uint64()
+        glop.lib().glop_scan_host_staging_size(a.handle, N, M, ctypes.byref(sz))
+        staging = torch.empty(int(sz.value), dtype=torch.uint8, device=dev)
+        hm_pinned = torch.empty((M, 2), dtype=torch.int32, pin_memory=True)
+        cnt = ctypes.c_uint64()
+        hp = host.data_ptr()
+        for i in range(2 + args.e2e_steps):
+            if i == 2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            rc = glop.lib().glop_scan_host(a.handle, hp, N, hm_pinned.data_ptr(), M, ctypes.byref(cnt),
+                                           staging.data_ptr(), staging.numel(), stream.cuda_stream)
+            assert rc == 0, rc
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(8.0 * N * args.e2e_steps * ws / dt / 1e9, 3), "unit": "Gbit/s",
+               "h2d_bytes_per_step": N, "d2h_bytes_per_step": 8 + 8 * M}
+        del hm, need
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    line = {
+        "metric": "Gbit/s scanned (8*N/t, Eq. 1)", "value": round(gbps, 3), "unit": "Gbit/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "text_bytes": N, "patterns": w.patterns.n, "matches": M,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "dp%d (independent shards)" % ws},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "note": "algorithmic bytes = text + halo re-reads + %d B/match + tile status; peak %s"
+                             % (rec * 4, which)},
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "hbm_input_frac": round(N / (avg_launch_ms / 1e3) / 1e9 / hbm, 4),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

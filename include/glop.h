@@ -1,0 +1,198 @@
+/*
+ * glop.h -- C ABI of the GB300 multi-pattern scan library (libglop.so).
+ *
+ * The library finds every occurrence of every pattern of a signature set in
+ * a byte buffer: the result is the set of (offset, pattern_id) pairs with
+ * pattern j equal to text[offset .. offset + |p_j|), sorted by offset then
+ * pattern id.  It is the first searching stage of the paper's log-processing
+ * library (Sec. 1, use case: rules in, logs in, the number of suspect
+ * events and their locations out) done by a failureless trie walked from
+ * every byte offset (Sec. 5), completed on the GPU so that results are exact.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are CUDA device pointers; all others are host
+ *    pointers.  Sizes are in bytes unless stated.
+ *  - The caller owns every buffer it passes (text, matches, count,
+ *    workspace); the library never frees them.  The library owns the
+ *    compiled automaton until glop_destroy().
+ *  - stream is a cudaStream_t (cast to void*); 0 is the legacy default stream.
+ *  - Argument errors are returned synchronously, before any work is queued.
+ *    Conditions found by the GPU (match overflow, a bounded wait that ran
+ *    out) are reported through *d_count and the workspace status word, read
+ *    with glop_scan_status().
+ *  - A handle is immutable after glop_compile() and may be scanned
+ *    concurrently from several streams, each with its own workspace.
+ *  - Every call on a machine without a usable CUDA device returns
+ *    GLOP_ECUDA; there is no CPU fallback.
+ */
+#ifndef GLOP_H
+#define GLOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glop_automaton *glop_handle; /* opaque */
+typedef void *glop_stream_t;                /* a cudaStream_t */
+
+typedef enum {
+    GLOP_OK = 0,
+    GLOP_EINVAL = 1,    /* bad argument (null pointer, zero-length pattern, size limits, ...) */
+    GLOP_ENOMEM = 2,    /* host or device allocation failed, or workspace too small */
+    GLOP_EOVERFLOW = 3, /* more matches than the capacity given; *d_count holds the true total */
+    GLOP_ECUDA = 4,     /* a CUDA runtime call failed or no device is usable */
+    GLOP_ETIMEOUT = 5,  /* a bounded wait inside a kernel ran out; results are incomplete */
+    GLOP_EBUSY = 6,     /* resource in use */
+    GLOP_EINTERNAL = 7  /* an internal consistency check failed */
+} glop_status;
+
+/* One match of glop_scan(): pattern pattern_id occurs at text[offset ...]. */
+typedef struct {
+    uint32_t offset;
+    uint32_t pattern_id;
+} glop_match;
+
+/* One match of glop_scan_batch(): offset is relative to the segment start. */
+typedef struct {
+    uint32_t segment;
+    uint32_t offset;
+    uint32_t pattern_id;
+} glop_batch_match;
+
+/* Compile options; a NULL pointer means all zero. */
+typedef struct {
+    /* 0: exact full-pattern matching.  K > 0: every pattern is cut to its
+     * first min(|p|, K) bytes before compiling -- the prefix (partial)
+     * matching of Sec. 1 and Sec. 5, whose paper setting is K = 8. */
+    uint32_t prefix_len;
+    /* Shared memory per thread block for transition rows staged on chip;
+     * 0 lets the library choose. */
+    uint32_t smem_budget_bytes;
+    uint32_t flags; /* reserved, must be 0 */
+} glop_compile_opts;
+
+/* Facts about a compiled automaton (glop_info_get). */
+typedef struct {
+    uint32_t n_patterns;
+    uint32_t min_pattern_len, max_pattern_len; /* after prefix cut */
+    uint32_t n_states;        /* trie states including the initial state */
+    uint32_t n_dense_states;  /* states with a full transition row (initial + branching) */
+    uint32_t n_chain_states;  /* states on unary chains, matched by byte comparison */
+    uint32_t n_classes;       /* alphabet classes of the transition rows */
+    uint32_t gram_len;        /* bytes hashed by the start filter; 0 = no filter */
+    uint32_t n_grams;         /* distinct gram_len-byte pattern prefixes */
+    uint32_t cum_ids;         /* pattern ids stored in per-state output lists */
+    uint64_t device_bytes;    /* device memory held by the handle */
+    double compile_ms;        /* host time of glop_compile */
+} glop_info;
+
+/*
+ * glop_compile -- build the automaton of a pattern set (Sec. 4, first phase;
+ * Sec. 5, failure transitions removed) and copy it to the current device.
+ *
+ * pattern_bytes   host, concatenated pattern bytes (any of the 256 values).
+ * pattern_offsets host, n_patterns + 1 non-decreasing offsets into
+ *                 pattern_bytes; pattern j is bytes [off[j], off[j+1]).
+ *                 Its id is j.  Duplicates are allowed and all reported.
+ * n_patterns      0 is valid (every scan then finds nothing); at most 2^31.
+ * opts            may be NULL.
+ * out             receives the handle; unchanged on error.
+ *
+ * Errors: GLOP_EINVAL for a zero-length pattern (after the prefix cut),
+ * decreasing offsets, a null pointer, or tables beyond 2^31 states;
+ * GLOP_ENOMEM; GLOP_ECUDA.  Synchronous: the handle is ready on return.
+ */
+glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_offsets, uint32_t n_patterns,
+                         const glop_compile_opts *opts, glop_handle *out);
+
+/* glop_info_get -- fill *info for handle h.  GLOP_EINVAL on null arguments. */
+glop_status glop_info_get(glop_handle h, glop_info *info);
+
+/* Longest pattern after the prefix cut: the overlap a caller needs between
+ * consecutive chunks of a stream (Sec. 4: at least the longest pattern - 1). */
+uint32_t glop_max_pattern_len(glop_handle h);
+
+/* glop_scan_workspace_size -- device workspace bytes glop_scan() needs for a
+ * text of text_len bytes (a few bytes per 4 KiB tile). */
+glop_status glop_scan_workspace_size(glop_handle h, uint64_t text_len, uint64_t *bytes);
+
+/*
+ * glop_scan -- every (offset, pattern_id) match in d_text[0, len), sorted by
+ * (offset, pattern_id), written to d_matches[0, min(count, capacity)).
+ *
+ * d_text       device, len bytes; any alignment (16-byte aligned is fastest).
+ * len          at most 2^32 - 1 (offsets are 32-bit).  0 is valid.
+ * d_matches    device, capacity entries (may be NULL when capacity is 0).
+ * d_count      device, one uint64_t: receives the total number of matches,
+ *              also when it exceeds capacity (then only the first capacity
+ *              matches in sorted order are written).
+ * d_workspace  device, at least glop_scan_workspace_size() bytes, 16-byte
+ *              aligned.  Must not be used by another scan until this one
+ *              has finished on the stream.
+ *
+ * Asynchronous on stream.  Returns GLOP_EINVAL / GLOP_ENOMEM (workspace too
+ * small) / GLOP_ECUDA synchronously; GPU-side conditions via
+ * glop_scan_status().
+ */
+glop_status glop_scan(glop_handle h, const uint8_t *d_text, uint64_t len, glop_match *d_matches, uint64_t capacity,
+                      uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream);
+
+/* glop_batch_workspace_size -- device workspace bytes for glop_scan_batch()
+ * over text_len bytes cut into n_segments segments. */
+glop_status glop_batch_workspace_size(glop_handle h, uint64_t text_len, uint32_t n_segments, uint64_t *bytes);
+
+/*
+ * glop_scan_batch -- the definition of glop_scan applied to every segment of
+ * one buffer (log files, packet payloads): segment s is
+ * d_text[d_seg_offsets[s], d_seg_offsets[s+1]); matches never cross a segment
+ * end; offsets are relative to the segment start; output sorted by
+ * (segment, offset, pattern_id).  One persistent launch covers all segments.
+ *
+ * d_seg_offsets device, n_segments + 1 non-decreasing values, the last at
+ *               most text_len; each segment at most 2^32 - 1 bytes.  Checked
+ *               on the GPU: malformed offsets make glop_scan_status() return
+ *               GLOP_EINVAL and write *d_count = 0.
+ * text_len      bytes of d_text covered by the segments.
+ * Other arguments as for glop_scan().
+ */
+glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
+                            uint32_t n_segments, glop_batch_match *d_matches, uint64_t capacity, uint64_t *d_count,
+                            void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream);
+
+/*
+ * glop_scan_status -- wait for stream, then report the outcome of the last
+ * scan that used d_workspace: GLOP_OK, GLOP_EOVERFLOW (more matches than
+ * capacity), GLOP_ETIMEOUT (a bounded in-kernel wait ran out), GLOP_EINVAL
+ * (malformed batch offsets) or GLOP_ECUDA.  If count is not NULL it receives
+ * the total match count.
+ */
+glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count);
+
+/*
+ * glop_scan_host -- glop_scan on HOST buffers, end to end: copies text to the
+ * device, scans, copies the count and the matches back, and waits for
+ * completion.  Device buffers come from d_staging (at least
+ * glop_scan_host_staging_size() bytes, caller-owned, 256-byte aligned).
+ * h_matches receives min(count, capacity) matches; *h_count the total.
+ * Pinned host memory gives the fastest copies.  Returns GLOP_EOVERFLOW when
+ * count > capacity (the first capacity matches are still delivered).
+ */
+glop_status glop_scan_host_staging_size(glop_handle h, uint64_t len, uint64_t capacity, uint64_t *bytes);
+glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, glop_match *h_matches,
+                           uint64_t capacity, uint64_t *h_count, void *d_staging, uint64_t staging_bytes,
+                           glop_stream_t stream);
+
+/* glop_destroy -- free the automaton's device memory.  No scan using h may
+ * still be in flight.  NULL is accepted. */
+glop_status glop_destroy(glop_handle h);
+
+/* Static description of a status code. */
+const char *glop_status_str(glop_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLOP_H */

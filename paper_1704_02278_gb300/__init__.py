@@ -1,0 +1,284 @@
+"""GB300 multi-pattern scan library -- Python binding of include/glop.h.
+
+Exact multi-pattern search over byte buffers: every (offset, pattern_id) with
+pattern ``pattern_id`` equal to ``text[offset : offset + len]``, sorted.  It is
+the first searching stage of the paper's GPU log-processing library (Sec. 1:
+rules and logs in, the count and locations of suspect events out), done by a
+failureless trie walked from every byte offset (Sec. 5) and completed on the
+GPU so that every reported match is exact.
+
+This module only marshals arguments: every step of a scan runs in the CUDA
+kernels of ``libglop.so``.  PyTorch provides device memory and streams.  There
+is no CPU fallback: without the built library or a CUDA device every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["Automaton", "GlopError", "lib", "library_path", "STATUS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libglop.so")
+_lib = None
+_lock = threading.Lock()
+
+STATUS = {0: "GLOP_OK", 1: "GLOP_EINVAL", 2: "GLOP_ENOMEM", 3: "GLOP_EOVERFLOW", 4: "GLOP_ECUDA",
+          5: "GLOP_ETIMEOUT", 6: "GLOP_EBUSY", 7: "GLOP_EINTERNAL"}
+OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
+
+# Exported symbols of include/glop.h
+SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_workspace_size", "glop_scan",
+           "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
+           "glop_scan_host", "glop_destroy", "glop_status_str"]
+
+
+class GlopError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__("%s%s" % (STATUS.get(code, "status %d" % code), (": " + what) if what else ""))
+        self.code = code
+
+
+class glop_compile_opts(ctypes.Structure):
+    _fields_ = [("prefix_len", ctypes.c_uint32), ("smem_budget_bytes", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class glop_info(ctypes.Structure):
+    _fields_ = [("n_patterns", ctypes.c_uint32), ("min_pattern_len", ctypes.c_uint32),
+                ("max_pattern_len", ctypes.c_uint32), ("n_states", ctypes.c_uint32),
+                ("n_dense_states", ctypes.c_uint32), ("n_chain_states", ctypes.c_uint32),
+                ("n_classes", ctypes.c_uint32), ("gram_len", ctypes.c_uint32), ("n_grams", ctypes.c_uint32),
+                ("cum_ids", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("compile_ms", ctypes.c_double)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """The loaded libglop.so; raises if it was not built (run ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libglop.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        L.glop_compile.restype = ctypes.c_int
+        L.glop_compile.argtypes = [vp, vp, u32, ctypes.POINTER(glop_compile_opts), ctypes.POINTER(vp)]
+        L.glop_info_get.restype = ctypes.c_int
+        L.glop_info_get.argtypes = [vp, ctypes.POINTER(glop_info)]
+        L.glop_max_pattern_len.restype = u32
+        L.glop_max_pattern_len.argtypes = [vp]
+        L.glop_scan_workspace_size.restype = ctypes.c_int
+        L.glop_scan_workspace_size.argtypes = [vp, u64, ctypes.POINTER(u64)]
+        L.glop_batch_workspace_size.restype = ctypes.c_int
+        L.glop_batch_workspace_size.argtypes = [vp, u64, u32, ctypes.POINTER(u64)]
+        L.glop_scan.restype = ctypes.c_int
+        L.glop_scan.argtypes = [vp, vp, u64, vp, u64, vp, vp, u64, vp]
+        L.glop_scan_batch.restype = ctypes.c_int
+        L.glop_scan_batch.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, u64, vp]
+        L.glop_scan_status.restype = ctypes.c_int
+        L.glop_scan_status.argtypes = [vp, vp, ctypes.POINTER(u64)]
+        L.glop_scan_host_staging_size.restype = ctypes.c_int
+        L.glop_scan_host_staging_size.argtypes = [vp, u64, u64, ctypes.POINTER(u64)]
+        L.glop_scan_host.restype = ctypes.c_int
+        L.glop_scan_host.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(u64), vp, u64, vp]
+        L.glop_destroy.restype = ctypes.c_int
+        L.glop_destroy.argtypes = [vp]
+        L.glop_status_str.restype = ctypes.c_char_p
+        L.glop_status_str.argtypes = [ctypes.c_int]
+        _lib = L
+        return L
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise GlopError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _pattern_csr(patterns):
+    if isinstance(patterns, tuple) and len(patterns) == 2:
+        return (np.ascontiguousarray(patterns[0], dtype=np.uint8), np.ascontiguousarray(patterns[1], dtype=np.uint64))
+    if hasattr(patterns, "buf") and hasattr(patterns, "offs"):
+        return (np.ascontiguousarray(patterns.buf, dtype=np.uint8), np.ascontiguousarray(patterns.offs, dtype=np.uint64))
+    pats = [bytes(p) for p in patterns]
+    offs = np.zeros(len(pats) + 1, dtype=np.uint64)
+    if pats:
+        offs[1:] = np.cumsum([len(p) for p in pats])
+    buf = np.frombuffer(b"".join(pats), dtype=np.uint8).copy() if pats else np.zeros(1, np.uint8)
+    return buf, offs
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Automaton:
+    """A compiled pattern set resident on the current CUDA device.
+
+    ``patterns``: a list of bytes, or (uint8 buffer, uint64 offsets[n+1]).
+    ``prefix_len``: 0 for exact patterns; K > 0 cuts every pattern to K bytes
+    (the paper's prefix matching uses K = 8).
+    """
+
+    def __init__(self, patterns, prefix_len: int = 0, smem_budget: int = 0):
+        L = lib()
+        buf, offs = _pattern_csr(patterns)
+        if buf.size == 0:
+            buf = np.zeros(1, np.uint8)
+        opts = glop_compile_opts(prefix_len, smem_budget, 0)
+        h = ctypes.c_void_p()
+        _check(L.glop_compile(buf.ctypes.data, offs.ctypes.data, len(offs) - 1, ctypes.byref(opts),
+                              ctypes.byref(h)), "glop_compile")
+        self._h = h
+        self.n_patterns = len(offs) - 1
+        self._ws = {}
+
+    # -- properties
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise GlopError(EINVAL, "automaton destroyed")
+        return self._h
+
+    @property
+    def info(self) -> dict:
+        inf = glop_info()
+        _check(lib().glop_info_get(self.handle, ctypes.byref(inf)), "glop_info_get")
+        return {k: getattr(inf, k) for k, _ in glop_info._fields_}
+
+    @property
+    def max_pattern_len(self) -> int:
+        return int(lib().glop_max_pattern_len(self.handle))
+
+    def workspace_bytes(self, text_len: int, n_segments: int | None = None) -> int:
+        v = ctypes.c_uint64()
+        if n_segments is None:
+            _check(lib().glop_scan_workspace_size(self.handle, text_len, ctypes.byref(v)), "workspace size")
+        else:
+            _check(lib().glop_batch_workspace_size(self.handle, text_len, n_segments, ctypes.byref(v)), "ws size")
+        return int(v.value)
+
+    def workspace(self, text_len: int, device, n_segments: int | None = None):
+        """A cached device workspace large enough for text_len bytes."""
+        torch = _torch()
+        need = self.workspace_bytes(text_len, n_segments)
+        key = (str(device), n_segments is not None)
+        ws = self._ws.get(key)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=device)
+            self._ws[key] = ws
+        return ws
+
+    # -- scans
+    def scan_into(self, text, matches, count, workspace=None, stream=None) -> None:
+        """Queue a scan of ``text`` (uint8 CUDA tensor) writing ``matches`` ((cap, 2) int32 CUDA
+        tensor) and ``count`` (int64 CUDA tensor of one element).  Asynchronous."""
+        n = text.numel()
+        ws = workspace if workspace is not None else self.workspace(n, text.device)
+        cap = matches.shape[0] if matches is not None else 0
+        _check(lib().glop_scan(self.handle, text.data_ptr() if n else None, n,
+                               matches.data_ptr() if cap else None, cap, count.data_ptr(),
+                               ws.data_ptr(), ws.numel(), _stream_handle(stream)), "glop_scan")
+
+    def scan(self, text, capacity: int | None = None, stream=None):
+        """All matches of a uint8 CUDA tensor: ((M, 2) int32 tensor of (offset, pattern_id), M).
+
+        The capacity is grown and the scan repeated when the first guess is too small."""
+        torch = _torch()
+        n = text.numel()
+        cap = capacity if capacity is not None else max(1024, n // 4)
+        count = torch.zeros(1, dtype=torch.int64, device=text.device)
+        while True:
+            m = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=text.device)
+            self.scan_into(text, m, count, stream=stream)
+            st = self.status(text.device, stream=stream)
+            total = int(count.item())
+            if total <= cap:
+                if st not in (OK,):
+                    raise GlopError(st, "scan")
+                return m[:total], total
+            if capacity is not None:
+                raise GlopError(EOVERFLOW, "%d matches > capacity %d" % (total, cap))
+            cap = total
+
+    def status(self, device, stream=None, batch: bool = False) -> int:
+        ws = self._ws.get((str(device), batch))
+        if ws is None:
+            return OK
+        cnt = ctypes.c_uint64()
+        return int(lib().glop_scan_status(ws.data_ptr(), _stream_handle(stream), ctypes.byref(cnt)))
+
+    def scan_batch_into(self, text, seg_offsets, matches, count, workspace=None, stream=None) -> None:
+        """Queue a batch scan: ``seg_offsets`` int64 CUDA tensor of n+1 offsets; ``matches`` (cap, 3) int32."""
+        n = text.numel()
+        nseg = seg_offsets.numel() - 1
+        ws = workspace if workspace is not None else self.workspace(n, text.device, nseg)
+        cap = matches.shape[0] if matches is not None else 0
+        _check(lib().glop_scan_batch(self.handle, text.data_ptr() if n else None, n, seg_offsets.data_ptr(), nseg,
+                                     matches.data_ptr() if cap else None, cap, count.data_ptr(), ws.data_ptr(),
+                                     ws.numel(), _stream_handle(stream)), "glop_scan_batch")
+
+    def scan_batch(self, text, seg_offsets, capacity: int | None = None, stream=None):
+        """All matches per segment: ((M, 3) int32 tensor of (segment, offset, pattern_id), M)."""
+        torch = _torch()
+        n = text.numel()
+        cap = capacity if capacity is not None else max(1024, n // 4)
+        count = torch.zeros(1, dtype=torch.int64, device=text.device)
+        while True:
+            m = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=text.device)
+            self.scan_batch_into(text, seg_offsets, m, count, stream=stream)
+            st = self.status(text.device, stream=stream, batch=True)
+            total = int(count.item())
+            if st == EINVAL:
+                raise GlopError(EINVAL, "malformed segment offsets")
+            if total <= cap:
+                if st != OK:
+                    raise GlopError(st, "scan_batch")
+                return m[:total], total
+            if capacity is not None:
+                raise GlopError(EOVERFLOW, "%d matches > capacity %d" % (total, cap))
+            cap = total
+
+    def scan_host(self, text: np.ndarray, capacity: int, staging=None, stream=None):
+        """End-to-end scan of a HOST uint8 array (pinned is fastest): copies in, scans, copies back.
+        Returns ((M, 2) uint32 numpy array, total count)."""
+        torch = _torch()
+        t = np.ascontiguousarray(text, dtype=np.uint8).reshape(-1)
+        need = ctypes.c_uint64()
+        _check(lib().glop_scan_host_staging_size(self.handle, t.size, capacity, ctypes.byref(need)), "staging")
+        if staging is None:
+            staging = torch.empty(int(need.value), dtype=torch.uint8, device="cuda")
+        out = np.empty((max(capacity, 1), 2), dtype=np.uint32)
+        cnt = ctypes.c_uint64()
+        rc = lib().glop_scan_host(self.handle, t.ctypes.data if t.size else None, t.size, out.ctypes.data, capacity,
+                                  ctypes.byref(cnt), staging.data_ptr(), staging.numel(), _stream_handle(stream))
+        if rc not in (OK, EOVERFLOW):
+            raise GlopError(rc, "glop_scan_host")
+        total = int(cnt.value)
+        return out[:min(total, capacity)], total
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().glop_destroy(self._h)
+            self._h = None
+        self._ws = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

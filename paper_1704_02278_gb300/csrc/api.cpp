@@ -1,0 +1,268 @@
+// api.cpp -- the C ABI of include/glop.h.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "compile.h"
+#include "glop.h"
+#include "scan.h"
+
+struct glop_automaton {
+    GlopDevAutomaton dev;  // descriptor with device pointers
+    void *blob = nullptr;  // one device allocation holding every table
+    uint64_t blob_bytes = 0;
+    int device = 0;
+    glop_info info{};
+    uint32_t smem_budget = 0;
+};
+
+namespace {
+
+uint64_t al(uint64_t x) { return (x + 255) / 256 * 256; }
+
+template <class T>
+uint64_t bytes_of(const std::vector<T> &v) {
+    return (uint64_t)v.size() * sizeof(T);
+}
+
+glop_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? GLOP_OK : GLOP_ECUDA; }
+
+}  // namespace
+
+extern "C" {
+
+const char *glop_status_str(glop_status s) {
+    switch (s) {
+        case GLOP_OK: return "ok";
+        case GLOP_EINVAL: return "invalid argument";
+        case GLOP_ENOMEM: return "out of memory";
+        case GLOP_EOVERFLOW: return "match capacity exceeded";
+        case GLOP_ECUDA: return "CUDA error";
+        case GLOP_ETIMEOUT: return "bounded wait timed out";
+        case GLOP_EBUSY: return "busy";
+        case GLOP_EINTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_offsets, uint32_t n_patterns,
+                         const glop_compile_opts *opts, glop_handle *out) {
+    if (!out || !pattern_offsets || (n_patterns && !pattern_bytes)) return GLOP_EINVAL;
+    if (opts && opts->flags) return GLOP_EINVAL;
+    auto t0 = std::chrono::steady_clock::now();
+    glop::HostAutomaton H;
+    std::string err;
+    int rc;
+    try {
+        rc = glop::compile_host(pattern_bytes, pattern_offsets, n_patterns, opts ? opts->prefix_len : 0, &H, &err);
+    } catch (const std::bad_alloc &) {
+        return GLOP_ENOMEM;
+    }
+    if (rc) return (glop_status)rc;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GLOP_ECUDA;
+
+    // one device blob; every array 256-byte aligned; chain bytes padded by 16 zero bytes
+    uint64_t o_cls = 0;
+    uint64_t o_rows = al(o_cls + 256);
+    uint64_t o_chain = al(o_rows + bytes_of(H.rows));
+    uint64_t o_cb = al(o_chain + bytes_of(H.chain));
+    uint64_t o_cum = al(o_cb + H.chain_bytes.size() + 16);
+    uint64_t o_ids = al(o_cum + bytes_of(H.cum_off));
+    uint64_t o_bm = al(o_ids + bytes_of(H.cum_ids) + 16);
+    uint64_t o_gr = al(o_bm + bytes_of(H.bitmap) + 16);
+    uint64_t total = al(o_gr + bytes_of(H.grams) + 16);
+    std::vector<uint8_t> host;
+    try {
+        host.assign(total, 0);
+    } catch (const std::bad_alloc &) {
+        return GLOP_ENOMEM;
+    }
+    std::memcpy(host.data() + o_cls, H.cls.data(), 256);
+    if (!H.rows.empty()) std::memcpy(host.data() + o_rows, H.rows.data(), bytes_of(H.rows));
+    if (!H.chain.empty()) std::memcpy(host.data() + o_chain, H.chain.data(), bytes_of(H.chain));
+    if (!H.chain_bytes.empty()) std::memcpy(host.data() + o_cb, H.chain_bytes.data(), H.chain_bytes.size());
+    std::memcpy(host.data() + o_cum, H.cum_off.data(), bytes_of(H.cum_off));
+    if (!H.cum_ids.empty()) std::memcpy(host.data() + o_ids, H.cum_ids.data(), bytes_of(H.cum_ids));
+    if (!H.bitmap.empty()) std::memcpy(host.data() + o_bm, H.bitmap.data(), bytes_of(H.bitmap));
+    if (!H.grams.empty()) std::memcpy(host.data() + o_gr, H.grams.data(), bytes_of(H.grams));
+
+    glop_automaton *h = new (std::nothrow) glop_automaton();
+    if (!h) return GLOP_ENOMEM;
+    if (cudaMalloc(&h->blob, total) != cudaSuccess) {
+        delete h;
+        cudaGetLastError();
+        return GLOP_ENOMEM;
+    }
+    if (cudaMemcpy(h->blob, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(h->blob);
+        delete h;
+        return GLOP_ECUDA;
+    }
+    uint8_t *base = reinterpret_cast<uint8_t *>(h->blob);
+    GlopDevAutomaton &D = h->dev;
+    D.n_states = H.n_states;
+    D.n_dense = H.n_dense;
+    D.n_classes = H.n_classes;
+    D.n_patterns = H.n_patterns;
+    D.min_len = H.min_len;
+    D.max_len = H.max_len;
+    D.gram_len = H.gram_len;
+    D.bm_log2 = H.bm_log2;
+    D.ht_log2 = H.ht_log2;
+    D.hot_lo = H.hot_lo;
+    D.cls = base + o_cls;
+    D.rows = reinterpret_cast<const int32_t *>(base + o_rows);
+    D.chain = reinterpret_cast<const GlopChain *>(base + o_chain);
+    D.chain_bytes = base + o_cb;
+    D.cum_off = reinterpret_cast<const uint32_t *>(base + o_cum);
+    D.cum_ids = reinterpret_cast<const uint32_t *>(base + o_ids);
+    D.bitmap = reinterpret_cast<const uint32_t *>(base + o_bm);
+    D.grams = reinterpret_cast<const GlopGramSlot *>(base + o_gr);
+    h->blob_bytes = total;
+    h->device = dev;
+    h->smem_budget = opts ? opts->smem_budget_bytes : 0;
+    glop_info &I = h->info;
+    I.n_patterns = H.n_patterns;
+    I.min_pattern_len = H.min_len;
+    I.max_pattern_len = H.max_len;
+    I.n_states = H.n_states;
+    I.n_dense_states = H.n_dense;
+    I.n_chain_states = H.n_states - H.n_dense;
+    I.n_classes = H.n_classes;
+    I.gram_len = H.gram_len;
+    I.n_grams = H.n_grams;
+    I.cum_ids = (uint32_t)H.cum_ids.size();
+    I.device_bytes = total;
+    I.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return GLOP_OK;
+}
+
+glop_status glop_info_get(glop_handle h, glop_info *info) {
+    if (!h || !info) return GLOP_EINVAL;
+    *info = h->info;
+    return GLOP_OK;
+}
+
+uint32_t glop_max_pattern_len(glop_handle h) { return h ? h->info.max_pattern_len : 0; }
+
+glop_status glop_scan_workspace_size(glop_handle h, uint64_t text_len, uint64_t *bytes) {
+    if (!h || !bytes) return GLOP_EINVAL;
+    *bytes = glop::workspace_bytes(text_len, false);
+    return GLOP_OK;
+}
+
+glop_status glop_batch_workspace_size(glop_handle h, uint64_t text_len, uint32_t n_segments, uint64_t *bytes) {
+    (void)n_segments;
+    if (!h || !bytes) return GLOP_EINVAL;
+    *bytes = glop::workspace_bytes(text_len, true);
+    return GLOP_OK;
+}
+
+static glop_status do_scan(glop_handle h, const uint8_t *d_text, uint64_t len, const uint64_t *seg, uint32_t n_seg,
+                           void *out, uint64_t capacity, uint64_t *d_count, void *ws, uint64_t ws_bytes,
+                           glop_stream_t stream) {
+    if (!h || !d_count || !ws || (len && !d_text) || (capacity && !out)) return GLOP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(ws) & 15) || (reinterpret_cast<uintptr_t>(d_count) & 7)) return GLOP_EINVAL;
+    if (ws_bytes < glop::workspace_bytes(len, seg != nullptr)) return GLOP_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GLOP_ECUDA;
+    if (dev != h->device) return GLOP_EINVAL;
+    glop::ScanLaunch L;
+    L.A = &h->dev;
+    L.text = d_text;
+    L.len = len;
+    L.seg = seg;
+    L.n_seg = n_seg;
+    L.out = out;
+    L.capacity = capacity;
+    L.d_count = d_count;
+    L.ws = ws;
+    L.ws_bytes = ws_bytes;
+    L.stream = reinterpret_cast<cudaStream_t>(stream);
+    L.smem_budget = h->smem_budget;
+    return (glop_status)glop::launch_scan(L);
+}
+
+glop_status glop_scan(glop_handle h, const uint8_t *d_text, uint64_t len, glop_match *d_matches, uint64_t capacity,
+                      uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream) {
+    if (len > 0xFFFFFFFFull) return GLOP_EINVAL;
+    if (d_matches && (reinterpret_cast<uintptr_t>(d_matches) & 7)) return GLOP_EINVAL;
+    return do_scan(h, d_text, len, nullptr, 0, d_matches, capacity, d_count, d_workspace, workspace_bytes, stream);
+}
+
+glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
+                            uint32_t n_segments, glop_batch_match *d_matches, uint64_t capacity, uint64_t *d_count,
+                            void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream) {
+    if (!d_seg_offsets || (reinterpret_cast<uintptr_t>(d_seg_offsets) & 7)) return GLOP_EINVAL;
+    if (d_matches && (reinterpret_cast<uintptr_t>(d_matches) & 3)) return GLOP_EINVAL;
+    return do_scan(h, d_text, text_len, d_seg_offsets, n_segments, d_matches, capacity, d_count, d_workspace,
+                   workspace_bytes, stream);
+}
+
+glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count) {
+    if (!d_workspace) return GLOP_EINVAL;
+    uint32_t hdr[8];
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
+    if (cudaMemcpy(hdr, d_workspace, sizeof hdr, cudaMemcpyDeviceToHost) != cudaSuccess) return GLOP_ECUDA;
+    uint64_t total;
+    std::memcpy(&total, hdr + 4, 8);
+    if (count) *count = total;
+    if (hdr[0] & glop::WS_EINVAL) return GLOP_EINVAL;
+    if (hdr[0] & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
+    if (hdr[0] & glop::WS_OVERFLOW) return GLOP_EOVERFLOW;
+    return GLOP_OK;
+}
+
+glop_status glop_scan_host_staging_size(glop_handle h, uint64_t len, uint64_t capacity, uint64_t *bytes) {
+    if (!h || !bytes) return GLOP_EINVAL;
+    *bytes = al(len) + al(capacity * sizeof(glop_match)) + 256 + glop::workspace_bytes(len, false);
+    return GLOP_OK;
+}
+
+glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, glop_match *h_matches,
+                           uint64_t capacity, uint64_t *h_count, void *d_staging, uint64_t staging_bytes,
+                           glop_stream_t stream) {
+    if (!h || !h_count || !d_staging || (len && !h_text) || (capacity && !h_matches)) return GLOP_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_staging) & 255) return GLOP_EINVAL;
+    uint64_t need = 0;
+    glop_scan_host_staging_size(h, len, capacity, &need);
+    if (staging_bytes < need) return GLOP_ENOMEM;
+    uint8_t *p = reinterpret_cast<uint8_t *>(d_staging);
+    uint8_t *d_text = p;
+    glop_match *d_m = reinterpret_cast<glop_match *>(p + al(len));
+    uint64_t *d_c = reinterpret_cast<uint64_t *>(p + al(len) + al(capacity * sizeof(glop_match)));
+    void *ws = p + al(len) + al(capacity * sizeof(glop_match)) + 256;
+    uint64_t ws_bytes = glop::workspace_bytes(len, false);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (len && cudaMemcpyAsync(d_text, h_text, len, cudaMemcpyHostToDevice, st) != cudaSuccess) return GLOP_ECUDA;
+    glop_status s = glop_scan(h, d_text, len, d_m, capacity, d_c, ws, ws_bytes, stream);
+    if (s != GLOP_OK) return s;
+    if (cudaMemcpyAsync(h_count, d_c, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GLOP_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
+    uint64_t n = *h_count < capacity ? *h_count : capacity;
+    if (n && cudaMemcpyAsync(h_matches, d_m, n * sizeof(glop_match), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return GLOP_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
+    uint32_t hdr0 = 0;
+    if (cudaMemcpy(&hdr0, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GLOP_ECUDA;
+    if (hdr0 & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
+    if (*h_count > capacity) return GLOP_EOVERFLOW;
+    return GLOP_OK;
+}
+
+glop_status glop_destroy(glop_handle h) {
+    if (!h) return GLOP_OK;
+    glop_status s = GLOP_OK;
+    if (h->blob) s = cuda_ok(cudaFree(h->blob));
+    delete h;
+    return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// glop_hash.h -- the start-filter hash, identical on host (compiler) and device.
+//
+// The start filter looks at the first gram_len (4..8) bytes at a text offset.
+// Every pattern is at least gram_len bytes long, so an offset can only start a
+// match if those bytes equal the first gram_len bytes of some pattern.  The
+// bytes are read as two little-endian words w0 (bytes 0..3) and w1 (bytes
+// 4..7, masked to gram_len - 4 bytes) and mixed multiplicatively.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define GLOP_HD __host__ __device__ __forceinline__
+#else
+#define GLOP_HD static inline
+#endif
+
+#define GLOP_HASH_M0 0x9E3779B1u
+#define GLOP_HASH_M1 0x85EBCA77u
+#define GLOP_HASH_M2 0x2C1B3C6Du
+
+// mask keeping the bytes of w1 that belong to a gram of gram_len bytes
+GLOP_HD uint32_t glop_w1_mask(uint32_t gram_len) {
+    return gram_len >= 8 ? 0xFFFFFFFFu : ((1u << (8u * (gram_len - 4u))) - 1u);
+}
+
+GLOP_HD uint32_t glop_gram_hash(uint32_t w0, uint32_t w1_masked) {
+    return (w0 * GLOP_HASH_M0) ^ (w1_masked * GLOP_HASH_M1);
+}
+
+// bit of the start-filter bitmap
+GLOP_HD uint32_t glop_bitmap_index(uint32_t h, uint32_t bm_log2) { return h >> (32u - bm_log2); }
+
+// first probe of the gram table (linear probing)
+GLOP_HD uint32_t glop_table_slot(uint32_t h, uint32_t ht_log2) {
+    return ((h ^ (h >> 15)) * GLOP_HASH_M2) >> (32u - ht_log2);
+}

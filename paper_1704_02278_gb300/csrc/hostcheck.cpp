@@ -1,0 +1,130 @@
+// hostcheck.cpp -- test-only host check of the compiled tables.
+//
+// Built into a separate library (libglop_hostcheck.so) that the CPU test
+// suite loads; libglop.so does not contain it and no scan entry point calls
+// it.  It runs the GPU walk's decision rules (start filter, gram table,
+// dense rows, chain comparison, per-state output lists) sequentially over
+// the compiler's host tables, so that the compiler can be checked against the
+// oracle on a machine without a GPU.  It is not a scan path of the library.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "compile.h"
+#include "glop_hash.h"
+
+using glop::HostAutomaton;
+
+namespace {
+
+uint32_t rd32(const uint8_t *p, uint64_t avail) {
+    uint32_t w = 0;
+    for (uint64_t k = 0; k < 4 && k < avail; ++k) w |= (uint32_t)p[k] << (8 * k);
+    return w;
+}
+
+// deepest terminal state reached from state s with the next text byte at pos
+uint32_t walk(const HostAutomaton &A, const uint8_t *text, uint32_t s, uint64_t pos, uint64_t end, uint32_t t) {
+    const uint32_t C = A.n_classes;
+    while (true) {
+        if (s < A.n_dense) {
+            if (pos >= end) return t;
+            int32_t e = A.rows[(size_t)s * C + A.cls[text[pos]]];
+            if (!e) return t;
+            s = (uint32_t)e & GLOP_STATE_MASK;
+            ++pos;
+            if ((uint32_t)e & GLOP_TERM) t = s;
+        } else {
+            const GlopChain &ch = A.chain[s - A.n_dense];
+            uint64_t lim = std::min<uint64_t>(ch.rem, end - pos);
+            uint64_t m = 0;
+            while (m < lim && text[pos + m] == A.chain_bytes[ch.off + m]) ++m;
+            uint32_t nchain = ch.rem - (ch.exit ? 1u : 0u);
+            if (ch.exit && m == ch.rem) {
+                uint32_t tt = A.chain[s + nchain - A.n_dense].term;
+                if (tt) t = tt;
+                s = ch.exit & GLOP_STATE_MASK;
+                if (ch.exit & GLOP_TERM) t = s;
+                pos += m;
+                continue;
+            }
+            uint32_t y = s + (uint32_t)std::min<uint64_t>(m, nchain);
+            uint32_t tt = A.chain[y - A.n_dense].term;
+            return tt ? tt : t;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Compile the pattern set, then report every (segment, offset, pattern_id)
+// of text by the GPU's decision rules.  stats[0..3] = n_states, n_dense,
+// n_classes, gram_len; stats[4] = offsets passing the start filter;
+// stats[5] = offsets found in the gram table.  Returns a glop_status value.
+int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat, uint32_t prefix_len,
+                        const uint8_t *text, const uint64_t *seg, uint32_t nseg, uint32_t **out, uint64_t *count,
+                        uint64_t *stats) {
+    *out = nullptr;
+    *count = 0;
+    HostAutomaton A;
+    std::string err;
+    int rc = glop::compile_host(pat, poff, npat, prefix_len, &A, &err);
+    if (rc) return rc;
+    std::vector<uint32_t> res;
+    uint64_t passed = 0, found = 0;
+    const uint32_t g = A.gram_len;
+    for (uint32_t sg = 0; sg < nseg && npat; ++sg) {
+        uint64_t lo = seg[sg], hi = seg[sg + 1];
+        for (uint64_t i = lo; i < hi; ++i) {
+            uint32_t s, t = 0;
+            uint64_t pos;
+            if (g) {
+                if (i + g > hi) continue;
+                uint32_t w0 = rd32(text + i, hi - i);
+                uint32_t w1 = rd32(text + i + 4, hi - i - 4) & glop_w1_mask(g);
+                uint32_t h = glop_gram_hash(w0, w1);
+                uint32_t bi = glop_bitmap_index(h, A.bm_log2);
+                if (!((A.bitmap[bi >> 5] >> (bi & 31)) & 1u)) continue;
+                ++passed;
+                uint32_t m = (1u << A.ht_log2) - 1, slot = glop_table_slot(h, A.ht_log2), v = 0;
+                while (A.grams[slot].val) {
+                    if (A.grams[slot].key_lo == w0 && A.grams[slot].key_hi == w1) { v = A.grams[slot].val; break; }
+                    slot = (slot + 1) & m;
+                }
+                if (!v) continue;
+                ++found;
+                s = v & GLOP_STATE_MASK;
+                if (v & GLOP_TERM) t = s;
+                pos = i + g;
+            } else {
+                s = 0;
+                pos = i;
+            }
+            t = walk(A, text, s, pos, hi, t);
+            for (uint32_t k = A.cum_off[t]; t && k < A.cum_off[t + 1]; ++k) {
+                res.push_back(sg);
+                res.push_back((uint32_t)(i - lo));
+                res.push_back(A.cum_ids[k]);
+            }
+        }
+    }
+    if (stats) {
+        stats[0] = A.n_states; stats[1] = A.n_dense; stats[2] = A.n_classes; stats[3] = A.gram_len;
+        stats[4] = passed; stats[5] = found;
+    }
+    *count = res.size() / 3;
+    if (!res.empty()) {
+        *out = (uint32_t *)std::malloc(res.size() * sizeof(uint32_t));
+        if (!*out) return 2;
+        std::memcpy(*out, res.data(), res.size() * sizeof(uint32_t));
+    }
+    return 0;
+}
+
+void glop_hostcheck_free(void *p) { std::free(p); }
+
+}  // extern "C"
