@@ -23,7 +23,8 @@ import numpy as np
 __all__ = ["Automaton", "GlopError", "lib", "library_path", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libglop.so")
+# GLOP_LIBRARY selects another build of the library (e.g. the bounds-checked debug build)
+_LIB_PATH = os.environ.get("GLOP_LIBRARY") or os.path.join(_HERE, "libglop.so")
 _lib = None
 _lock = threading.Lock()
 

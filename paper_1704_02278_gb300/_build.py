@@ -92,6 +92,24 @@ def build_lib(force: bool = False) -> str:
     return LIB
 
 
+def build_checked_lib(out_path: str) -> str:
+    """A debug build of libglop.so with every global index bounds-checked (-DGLOP_BOUNDS_CHECK)."""
+    objs = []
+    jobs = []
+    for src_name in CUDA_SOURCES + HOST_SOURCES:
+        src = os.path.join(CSRC, src_name)
+        obj = out_path + "." + src_name + ".o"
+        objs.append(obj)
+        flags = NVCC_FLAGS + ["-DGLOP_BOUNDS_CHECK"] if src_name.endswith(".cu") else \
+            ["-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+        jobs.append(([nvcc(), *flags, "-c", src, "-o", obj], obj + ".log"))
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        list(ex.map(lambda j: _run(*j), jobs))
+    _run([nvcc(), "-shared", *ARCH, "-o", out_path, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread"],
+         out_path + ".link.log")
+    return out_path
+
+
 def build_hostcheck(force: bool = False) -> str:
     """Compile the test-only host check (g++, no CUDA)."""
     srcs = [os.path.join(CSRC, "compile.cpp"), os.path.join(CSRC, "hostcheck.cpp")]

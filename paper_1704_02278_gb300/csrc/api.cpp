@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -66,12 +67,22 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return GLOP_ECUDA;
 
-    // one device blob; every array 256-byte aligned; chain bytes padded by 16 zero bytes
+    // dense rows as uint16 (state | 0x8000 when terminal) when every state id fits in 15 bits
+    const bool row16 = H.n_states <= 0x7FFF;
+    std::vector<uint16_t> rows16;
+    if (row16) {
+        rows16.resize(H.rows.size());
+        for (size_t i = 0; i < H.rows.size(); ++i) {
+            const uint32_t e = (uint32_t)H.rows[i];
+            rows16[i] = (uint16_t)((e & GLOP_STATE_MASK) | ((e & GLOP_TERM) ? 0x8000u : 0u));
+        }
+    }
+    const uint64_t rows_bytes = row16 ? bytes_of(rows16) : bytes_of(H.rows);
+    // one device blob; every array 256-byte aligned and followed by at least 16 spare bytes
     uint64_t o_cls = 0;
     uint64_t o_rows = al(o_cls + 256);
-    uint64_t o_chain = al(o_rows + bytes_of(H.rows));
-    uint64_t o_cb = al(o_chain + bytes_of(H.chain));
-    uint64_t o_cum = al(o_cb + H.chain_bytes.size() + 16);
+    uint64_t o_chain = al(o_rows + rows_bytes + 16);
+    uint64_t o_cum = al(o_chain + bytes_of(H.chain) + 16);
     uint64_t o_ids = al(o_cum + bytes_of(H.cum_off));
     uint64_t o_bm = al(o_ids + bytes_of(H.cum_ids) + 16);
     uint64_t o_gr = al(o_bm + bytes_of(H.bitmap) + 16);
@@ -83,9 +94,9 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
         return GLOP_ENOMEM;
     }
     std::memcpy(host.data() + o_cls, H.cls.data(), 256);
-    if (!H.rows.empty()) std::memcpy(host.data() + o_rows, H.rows.data(), bytes_of(H.rows));
+    if (rows_bytes) std::memcpy(host.data() + o_rows, row16 ? (const void *)rows16.data() : (const void *)H.rows.data(),
+                                rows_bytes);
     if (!H.chain.empty()) std::memcpy(host.data() + o_chain, H.chain.data(), bytes_of(H.chain));
-    if (!H.chain_bytes.empty()) std::memcpy(host.data() + o_cb, H.chain_bytes.data(), H.chain_bytes.size());
     std::memcpy(host.data() + o_cum, H.cum_off.data(), bytes_of(H.cum_off));
     if (!H.cum_ids.empty()) std::memcpy(host.data() + o_ids, H.cum_ids.data(), bytes_of(H.cum_ids));
     if (!H.bitmap.empty()) std::memcpy(host.data() + o_bm, H.bitmap.data(), bytes_of(H.bitmap));
@@ -116,11 +127,12 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
     D.ht_log2 = H.ht_log2;
     D.hot_lo = H.hot_lo;
     D.cls = base + o_cls;
-    D.rows = reinterpret_cast<const int32_t *>(base + o_rows);
+    D.rows = base + o_rows;
+    D.row16 = row16 ? 1u : 0u;
     D.chain = reinterpret_cast<const GlopChain *>(base + o_chain);
-    D.chain_bytes = base + o_cb;
     D.cum_off = reinterpret_cast<const uint32_t *>(base + o_cum);
     D.cum_ids = reinterpret_cast<const uint32_t *>(base + o_ids);
+    D.n_cum_ids = (uint32_t)H.cum_ids.size();
     D.bitmap = reinterpret_cast<const uint32_t *>(base + o_bm);
     D.grams = reinterpret_cast<const GlopGramSlot *>(base + o_gr);
     h->blob_bytes = total;
@@ -207,13 +219,17 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
 
 glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count) {
     if (!d_workspace) return GLOP_EINVAL;
-    uint32_t hdr[8];
+    uint32_t hdr[16];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
     if (cudaMemcpy(hdr, d_workspace, sizeof hdr, cudaMemcpyDeviceToHost) != cudaSuccess) return GLOP_ECUDA;
     uint64_t total;
     std::memcpy(&total, hdr + 4, 8);
     if (count) *count = total;
+    if (hdr[0] & glop::WS_INTERNAL) {
+        std::fprintf(stderr, "glop: internal check failed at site %u (value %u)\n", hdr[11], hdr[12]);
+        return GLOP_EINTERNAL;
+    }
     if (hdr[0] & glop::WS_EINVAL) return GLOP_EINVAL;
     if (hdr[0] & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
     if (hdr[0] & glop::WS_OVERFLOW) return GLOP_EOVERFLOW;

@@ -166,27 +166,35 @@ int compile_host(const uint8_t *bytes, const uint64_t *offs, uint32_t n, uint32_
         for (uint32_t c = first_child[dense_nodes[d]]; c != NIL; c = next_sib[c])
             A.rows[(size_t)d * C + A.cls[ebyte[c]]] = (int32_t)enc(c);
 
-    // ---- chains ----
+    // ---- chains, cut into pieces of at most 16 states ----
     A.chain.resize(N - A.n_dense);
     for (auto &ch : chains) {
-        uint32_t L = (uint32_t)ch.size();
-        uint32_t base = (uint32_t)A.chain_bytes.size();
-        for (uint32_t k = 1; k < L; ++k) A.chain_bytes.push_back(ebyte[ch[k]]);
-        uint32_t last = ch[L - 1], exit = 0, has_exit = 0;
-        if (first_child[last] != NIL) {
-            uint32_t d = first_child[last];
-            A.chain_bytes.push_back(ebyte[d]);
-            exit = enc(d);
-            has_exit = 1;
-        }
+        const uint32_t L = (uint32_t)ch.size();
+        const uint32_t last = ch[L - 1];
+        const uint32_t dense_child = first_child[last];  // NIL or a dense state
         uint32_t term = 0;
         for (uint32_t k = 0; k < L; ++k) {
             if (terminal(ch[k])) term = nid[ch[k]];
-            GlopChain &g = A.chain[nid[ch[k]] - A.n_dense];
-            g.off = base + k;
-            g.rem = (L - 1 - k) + has_exit;
+            const uint32_t p0 = k / 16 * 16, p1 = std::min(L, p0 + 16);  // piece [p0, p1)
+            const bool final_piece = (p1 == L);
+            uint32_t exit = 0, exit_byte = 0, has_exit = 0;
+            if (!final_piece) { exit = enc(ch[p1]); exit_byte = ebyte[ch[p1]]; has_exit = 1; }
+            else if (dense_child != NIL) { exit = enc(dense_child); exit_byte = ebyte[dense_child]; has_exit = 1; }
+            GlopChain g;
+            std::memset(&g, 0, sizeof g);
+            uint8_t b[16] = {0};
+            uint32_t nb = 0;
+            for (uint32_t x = k + 1; x < p1; ++x) b[nb++] = ebyte[ch[x]];
+            if (has_exit) b[nb++] = (uint8_t)exit_byte;
+            std::memcpy(g.inl, b, 16);
             g.exit = exit;
             g.term = term;
+            uint16_t tm = 0;
+            for (uint32_t x = k; x < p1; ++x) if (terminal(ch[x])) tm |= (uint16_t)(1u << (x - k));
+            g.termmask = tm;
+            g.nst = (uint8_t)(p1 - 1 - k);
+            g.rem = (uint8_t)(p1 - 1 - k + has_exit);
+            A.chain[nid[ch[k]] - A.n_dense] = g;
         }
     }
 

@@ -18,7 +18,6 @@ struct HostAutomaton {
     std::vector<uint8_t> cls;             // 256
     std::vector<int32_t> rows;            // n_dense * n_classes
     std::vector<GlopChain> chain;         // n_states - n_dense
-    std::vector<uint8_t> chain_bytes;
     std::vector<uint32_t> cum_off;        // n_states + 1
     std::vector<uint32_t> cum_ids;
     std::vector<uint32_t> bitmap;         // (1 << bm_log2) / 32 words

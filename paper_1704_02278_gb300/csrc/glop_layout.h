@@ -25,14 +25,20 @@
 #define GLOP_TERM 0x80000000u
 #define GLOP_STATE_MASK 0x7FFFFFFFu
 
-// per chain state: remaining chain bytes after this state, the exit into a
-// dense state, and the deepest terminal state of the chain up to this state
+// Per chain state (32 bytes, one sector).  A chain is cut into pieces of at
+// most 16 states; the record of a state holds, inline, every byte still to be
+// compared in its piece (the bytes leading to the later states of the piece,
+// then the byte of the exit), so one load resolves a chain step.
 struct GlopChain {
-    uint32_t off;   // index into chain_bytes of the byte that follows this state
-    uint32_t rem;   // remaining bytes: chain bytes after this state, plus 1 if the chain exits
-    uint32_t exit;  // dense state entered after the last chain byte (| GLOP_TERM), 0 = leaf-ended chain
-    uint32_t term;  // deepest terminal state among the chain's states up to this one, 0 = none
+    uint32_t inl[4];    // bytes to compare after this state, little-endian, zero padded
+    uint32_t exit;      // state entered after the piece (| GLOP_TERM): next piece or a dense state; 0 = none
+    uint32_t term;      // deepest terminal state of the chain from its first state up to this one, 0 = none
+    uint16_t termmask;  // bit k: the state k places after this one in the piece is terminal (bit 0: this state)
+    uint8_t rem;        // bytes to compare: states after this one in the piece, plus 1 if there is an exit
+    uint8_t nst;        // states after this one in the piece
+    uint32_t pad;
 };
+static_assert(sizeof(GlopChain) == 32, "a chain record is one 32-byte sector");
 
 // slot of the gram table: the state reached from the initial state by the
 // first gram_len bytes of some pattern
@@ -41,6 +47,7 @@ struct GlopGramSlot {
     uint32_t val;             // state | GLOP_TERM, 0 = empty slot
     uint32_t pad;
 };
+static_assert(sizeof(GlopGramSlot) == 16, "a gram slot is one 16-byte load");
 
 // Offsets (bytes) of the arrays inside one device allocation, and sizes.
 struct GlopDevAutomaton {
@@ -51,11 +58,12 @@ struct GlopDevAutomaton {
     uint32_t ht_log2;      // gram table has 1 << ht_log2 slots
     uint32_t hot_lo;       // first dense state worth staging on chip (depth >= gram_len)
     const uint8_t *cls;            // [256] byte -> class
-    const int32_t *rows;           // [n_dense * n_classes]
+    const void *rows;              // [n_dense * n_classes], see row16
     const GlopChain *chain;        // [n_states - n_dense]
-    const uint8_t *chain_bytes;
+    uint32_t row16;                // 1: rows are uint16 (state | 0x8000 when terminal), else int32
     const uint32_t *cum_off;       // [n_states + 1] output list of each state
     const uint32_t *cum_ids;       // pattern ids, ascending within a list
+    uint32_t n_cum_ids;            // entries of cum_ids
     const uint32_t *bitmap;        // [(1 << bm_log2) / 32]
     const GlopGramSlot *grams;     // [1 << ht_log2]
 };

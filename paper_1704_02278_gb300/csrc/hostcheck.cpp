@@ -25,12 +25,18 @@ uint32_t rd32(const uint8_t *p, uint64_t avail) {
     return w;
 }
 
+struct WalkStats {
+    uint64_t dense_steps = 0, chain_entries = 0, chain_bytes = 0, hot_steps = 0;
+};
+
 // deepest terminal state reached from state s with the next text byte at pos
-uint32_t walk(const HostAutomaton &A, const uint8_t *text, uint32_t s, uint64_t pos, uint64_t end, uint32_t t) {
+uint32_t walk(const HostAutomaton &A, const uint8_t *text, uint32_t s, uint64_t pos, uint64_t end, uint32_t t,
+              WalkStats &ws) {
     const uint32_t C = A.n_classes;
     while (true) {
         if (s < A.n_dense) {
             if (pos >= end) return t;
+            ++ws.dense_steps;
             int32_t e = A.rows[(size_t)s * C + A.cls[text[pos]]];
             if (!e) return t;
             s = (uint32_t)e & GLOP_STATE_MASK;
@@ -38,21 +44,29 @@ uint32_t walk(const HostAutomaton &A, const uint8_t *text, uint32_t s, uint64_t 
             if ((uint32_t)e & GLOP_TERM) t = s;
         } else {
             const GlopChain &ch = A.chain[s - A.n_dense];
+            ++ws.chain_entries;
+            uint8_t inl[16];
+            std::memcpy(inl, ch.inl, 16);
             uint64_t lim = std::min<uint64_t>(ch.rem, end - pos);
             uint64_t m = 0;
-            while (m < lim && text[pos + m] == A.chain_bytes[ch.off + m]) ++m;
-            uint32_t nchain = ch.rem - (ch.exit ? 1u : 0u);
+            while (m < lim && text[pos + m] == inl[m]) ++m;
+            ws.chain_bytes += m + (m < lim ? 1 : 0);
+            uint32_t r = (uint32_t)std::min<uint64_t>(m, ch.nst);
+            uint32_t tm = ch.termmask & ((2u << r) - 1u);
+            if (tm) {
+                uint32_t hb = 31;
+                while (!((tm >> hb) & 1u)) --hb;
+                t = s + hb;
+            } else if (ch.term) {
+                t = ch.term;
+            }
             if (ch.exit && m == ch.rem) {
-                uint32_t tt = A.chain[s + nchain - A.n_dense].term;
-                if (tt) t = tt;
                 s = ch.exit & GLOP_STATE_MASK;
                 if (ch.exit & GLOP_TERM) t = s;
                 pos += m;
                 continue;
             }
-            uint32_t y = s + (uint32_t)std::min<uint64_t>(m, nchain);
-            uint32_t tt = A.chain[y - A.n_dense].term;
-            return tt ? tt : t;
+            return t;
         }
     }
 }
@@ -64,7 +78,9 @@ extern "C" {
 // Compile the pattern set, then report every (segment, offset, pattern_id)
 // of text by the GPU's decision rules.  stats[0..3] = n_states, n_dense,
 // n_classes, gram_len; stats[4] = offsets passing the start filter;
-// stats[5] = offsets found in the gram table.  Returns a glop_status value.
+// stats[5] = offsets found in the gram table; stats[6..8] = dense-row steps,
+// chain entries and chain bytes compared by all walks; stats[9] = offsets
+// with at least one match.  Returns a glop_status value.
 int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat, uint32_t prefix_len,
                         const uint8_t *text, const uint64_t *seg, uint32_t nseg, uint32_t **out, uint64_t *count,
                         uint64_t *stats) {
@@ -75,7 +91,8 @@ int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat,
     int rc = glop::compile_host(pat, poff, npat, prefix_len, &A, &err);
     if (rc) return rc;
     std::vector<uint32_t> res;
-    uint64_t passed = 0, found = 0;
+    uint64_t passed = 0, found = 0, matched = 0;
+    WalkStats wst;
     const uint32_t g = A.gram_len;
     for (uint32_t sg = 0; sg < nseg && npat; ++sg) {
         uint64_t lo = seg[sg], hi = seg[sg + 1];
@@ -104,7 +121,8 @@ int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat,
                 s = 0;
                 pos = i;
             }
-            t = walk(A, text, s, pos, hi, t);
+            t = walk(A, text, s, pos, hi, t, wst);
+            if (t) ++matched;
             for (uint32_t k = A.cum_off[t]; t && k < A.cum_off[t + 1]; ++k) {
                 res.push_back(sg);
                 res.push_back((uint32_t)(i - lo));
@@ -115,6 +133,7 @@ int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat,
     if (stats) {
         stats[0] = A.n_states; stats[1] = A.n_dense; stats[2] = A.n_classes; stats[3] = A.gram_len;
         stats[4] = passed; stats[5] = found;
+        stats[6] = wst.dense_steps; stats[7] = wst.chain_entries; stats[8] = wst.chain_bytes; stats[9] = matched;
     }
     *count = res.size() / 3;
     if (!res.empty()) {

@@ -1,30 +1,37 @@
-// scan.cu -- the GB300 scan kernels.
+// scan.cu -- the GB300 scan kernel.
 //
 // One walk of the failureless trie starts at every text offset (Sec. 5: one
-// thread per character, a mismatch ends the walk).  Here a thread block is a
-// persistent set of independent "groups" of 256 threads; a group takes 4 KiB
-// tiles of the text from a global ticket counter and, per tile:
+// thread per character; a mismatch ends the walk).  The kernel is persistent
+// and cooperative (one 1024-thread block per SM) and runs in two phases.
 //
-//  1. the tile plus a halo of at least (longest pattern - 1) bytes arrives in
-//     shared memory by a TMA bulk copy issued one tile ahead (double buffer);
-//     the halo is the chunk overlap of Sec. 4, so no match is lost at a tile
-//     boundary, and a tile only reports matches that start inside it;
-//  2. each thread takes 16 consecutive start offsets, reads their bytes from
-//     two 16-byte shared-memory vectors and tests the first gram_len bytes of
-//     every offset against a bitmap of pattern prefixes (start filter);
-//  3. surviving offsets are compacted per warp (ballot-free prefix sums of
-//     popc) into a queue in offset order and walked densely: gram table ->
-//     state at depth gram_len, then dense rows (hot rows in shared memory,
-//     the rest through the read-only path from L2) and unary chains matched
-//     by 4-byte comparisons; the deepest terminal state of the walk names the
-//     sorted list of every pattern found at that offset (nested patterns);
-//  4. per-thread match counts are scanned in the group, the tile's global
-//     output position comes from a decoupled look-back over tile order, and
-//     every thread writes its matches in (offset, pattern id) order.
+// Phase A -- walk.  Warp 0 is a producer: it takes 31 KiB chunks of the text
+// from a global ticket counter and brings each, plus a halo of at least
+// (longest pattern - 1) bytes, into a 3-slot shared-memory ring with one TMA
+// bulk copy (L2 evict-first: the text is read once).  The halo is the chunk
+// overlap of Sec. 4: a chunk reports only matches that start inside it, and
+// no match is lost at a boundary.  Warps 1..31 are consumers; consumer w owns
+// the w-th 1 KiB sub-tile of every chunk, so consumers never wait on each
+// other, only on the ring.  Per sub-tile a lane takes 32 consecutive start
+// offsets, reads their bytes from shared memory as 16-byte vectors and tests
+// the first gram_len bytes of each against a bitmap of pattern prefixes.
+// Survivors are compacted across the warp with shuffles (in offset order) and
+// walked 32 at a time: gram table -> state at depth gram_len -> dense rows
+// (staged in shared memory when they fit) and unary chains (one 32-byte
+// record per step, bytes inline).  The deepest terminal state of a walk names
+// the sorted list of all patterns that occur at that offset (nested patterns
+// included).  A sub-tile writes compact (offset, state) records into its
+// block's scratch slice plus a descriptor (records, match count).
+//
+// Phase B -- ordered output.  After a grid-wide barrier every block sums the
+// match counts of a static range of sub-tiles; after a second barrier each
+// block knows where its range starts in the sorted output and expands its
+// records into (offset, pattern id) pairs with coalesced warp-wide writes.  A
+// sub-tile whose records did not fit the scratch slice is walked again here
+// and written directly, so results are exact for any input.
 //
 // There is no failure transition anywhere (Sec. 4 explains why they diverge
-// on SIMT hardware) and no floating point.  Every spin wait is bounded by a
-// clock budget; running out sets a flag in the workspace header.
+// on SIMT hardware) and no floating point.  Every wait is bounded by a clock
+// budget; running out sets a flag in the workspace header.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,20 +45,32 @@ namespace glop {
 
 namespace {
 
-constexpr uint32_t GT = kGroupThreads;
-constexpr uint32_t KOFF = kOffsetsPerThread;
-constexpr uint32_t TILE = kTile;
-constexpr uint32_t WARPS_G = GT / 32;
-constexpr uint32_t SEGCAP = 128;
+constexpr uint32_t SUB = kSubTile;
+constexpr uint32_t NCONS = kConsumers;
+constexpr uint32_t CHUNK = kChunk;
+constexpr uint32_t NSTAGE = 3;
+constexpr uint32_t THREADS = 32 * (NCONS + 1);
+constexpr uint32_t SEGW = 32;  // segment boundaries kept on chip per sub-tile
 constexpr uint32_t HALO_CAP = 1024;
+constexpr uint32_t PB = 4096;  // sub-tiles per phase-B piece
 constexpr uint32_t FULL = 0xFFFFFFFFu;
-constexpr unsigned long long FLAG_AGG = 1ull << 62, FLAG_PRE = 2ull << 62, VAL_MASK = (1ull << 62) - 1;
+constexpr unsigned long long END_TICKET = ~0ull;
+constexpr uint32_t REC_OVERFLOW = 0xFFFFFFFFu;
 
-struct GroupMisc {
-    unsigned long long mbar[2];
-    unsigned long long base;
-    unsigned long long tick[2];
-    uint32_t abort, seg_a, seg_L, seg_fallback;
+struct SubDesc {
+    uint32_t rec_start, n_rec;  // absolute record index; n_rec == REC_OVERFLOW: records not stored
+    unsigned long long n_match;
+};
+
+struct CtaMisc {
+    unsigned long long full[NSTAGE], empty[NSTAGE];
+    unsigned long long slot_tile[NSTAGE];
+    uint32_t slot_nstage[NSTAGE];
+    uint32_t rec_cursor;
+    uint32_t pad;
+    unsigned long long red[32];
+    unsigned long long segl[32][SEGW + 1];
+    uint32_t seg_a[32], seg_L[32];
 };
 
 struct KParams {
@@ -64,41 +83,41 @@ struct KParams {
     uint64_t cap;
     unsigned long long *d_count;
     uint32_t *hdr;
-    unsigned long long *tstat;
+    SubDesc *desc;
+    unsigned long long *sums;
     const uint32_t *tile_seg;
-    uint64_t n_tiles;
-    uint32_t halo, tbuf, hot_n, grams_in_smem, ngroups, aligned;
-    uint32_t off_bitmap, off_grams, off_rows, off_groups, group_bytes;
+    uint32_t *records;
+    uint32_t rec_cap_cta;  // record slots per block
+    uint64_t rec_slots;    // record slots in the workspace
+    uint64_t n_sub, n_chunks;
+    uint32_t halo, slot_bytes, hot_n, grams_in_smem, aligned;
+    uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring;
     long long spin_budget;
 };
 
 // ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// one bulk copy global -> shared completing on bar; bytes multiple of 16, both addresses 16-byte aligned
+// one bulk copy global -> shared completing on bar (16-byte aligned addresses,
+// size a multiple of 16); the text is streamed once, so it is evict-first in L2
 __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar) {
-    if (bytes) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_addr(dst)),
-            "l"(src), "r"(bytes), "r"(smem_addr(bar))
-            : "memory");
-    } else {
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity) {
@@ -111,7 +130,6 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
     return ok != 0;
 }
 
-// bounded wait; false when the budget ran out
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, long long budget) {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
@@ -119,24 +137,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     return true;
 }
 
-__device__ __forceinline__ void group_bar(uint32_t id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(GT) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t ld_relaxed32(const uint32_t *p) {
+__device__ __forceinline__ uint32_t ld_acquire32(const uint32_t *p) {
     uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src) {
+    uint32_t lo = __shfl_sync(FULL, (uint32_t)v, src), hi = __shfl_sync(FULL, (uint32_t)(v >> 32), src);
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 __device__ __forceinline__ unsigned long long shfl_up64(unsigned long long v, int d) {
@@ -144,469 +153,678 @@ __device__ __forceinline__ unsigned long long shfl_up64(unsigned long long v, in
     return ((unsigned long long)hi << 32) | lo;
 }
 
-__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long v, int d) {
-    uint32_t lo = __shfl_xor_sync(FULL, (uint32_t)v, d), hi = __shfl_xor_sync(FULL, (uint32_t)(v >> 32), d);
-    return ((unsigned long long)hi << 32) | lo;
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+    for (int d = 16; d; d >>= 1) {
+        uint32_t lo = __shfl_xor_sync(FULL, (uint32_t)v, d), hi = __shfl_xor_sync(FULL, (uint32_t)(v >> 32), d);
+        v += ((unsigned long long)hi << 32) | lo;
+    }
+    return v;
 }
 
-// largest k in [0, L] with e[k] <= x (e sorted, e[0] <= x assumed by the caller or k = 0)
-__device__ __forceinline__ uint32_t seg_find_smem(const unsigned long long *e, uint32_t L, unsigned long long x) {
-    uint32_t lo = 0, hi = L;  // invariant: answer in [lo, hi]
-    while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (e[mid] <= x) lo = mid; else hi = mid - 1;
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t u = __shfl_up_sync(FULL, v, d);
+        if (lane >= (uint32_t)d) v += u;
     }
-    return lo;
+    return v;
 }
 
-__device__ __forceinline__ uint32_t seg_find_global(const uint64_t *seg, uint32_t lo, uint32_t hi, uint64_t x) {
-    while (lo < hi) {
-        uint32_t mid = (lo + hi + 1) >> 1;
-        if (__ldg((const unsigned long long *)seg + mid) <= x) lo = mid; else hi = mid - 1;
+// the lane holding item i: the largest lane L with excl(L) <= i (excl non-decreasing, excl(0) = 0)
+__device__ __forceinline__ uint32_t owner_of(uint32_t excl, uint32_t i) {
+    uint32_t o = 0;
+#pragma unroll
+    for (uint32_t d = 16; d; d >>= 1) {
+        const uint32_t e = __shfl_sync(FULL, excl, o + d);
+        if (e <= i) o += d;
     }
-    return lo;
+    return o;
+}
+
+// A broken internal invariant: flag it with the site, never touch the memory.
+__device__ __noinline__ void fail_check(uint32_t *hdr, uint32_t site, uint32_t value) {
+    if (atomicOr(hdr, WS_INTERNAL) & WS_INTERNAL) return;
+    hdr[11] = site;
+    hdr[12] = value;
+}
+
+// Debug builds (-DGLOP_BOUNDS_CHECK) check every global index against its
+// array before the access; a failed check records its site and skips it.
+#ifdef GLOP_BOUNDS_CHECK
+#define GLOP_CK(hdr, cond, site, val) if (!(cond)) fail_check((hdr), (site), (uint32_t)(val)); else
+#define GLOP_BAIL(hdr, cond, site, val, ret) \
+    if (!(cond)) { fail_check((hdr), (site), (uint32_t)(val)); return ret; }
+#else
+#define GLOP_CK(hdr, cond, site, val)
+#define GLOP_BAIL(hdr, cond, site, val, ret)
+#endif
+
+// bounded grid-wide barrier (the launch is cooperative: every block is resident)
+__device__ void grid_sync(uint32_t *ctr, uint32_t nblocks, long long budget, uint32_t *hdr) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        long long t0 = clock64();
+        while (ld_acquire32(ctr) < nblocks) {
+            if (clock64() - t0 > budget) { atomicOr(hdr, WS_TIMEOUT); break; }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- the walk
-struct TileView {
-    const uint8_t *buf;      // staged bytes of the tile (shared memory)
-    const uint8_t *gtext;    // the same bytes in global memory (text + tile start)
-    uint32_t n_stage;        // staged bytes
+struct TextView {
+    const uint8_t *buf;    // staged bytes of the sub-tile (shared memory), or nullptr
+    const uint8_t *gtext;  // the same bytes in global memory
+    uint32_t n_stage;      // bytes available in buf
+#ifdef GLOP_BOUNDS_CHECK
+    uint64_t avail;        // text bytes from gtext to the end of the text
+    uint32_t *hdr;
+#endif
 };
 
-__device__ __forceinline__ uint32_t tile_byte(const TileView &v, uint32_t pos) {
-    return pos < v.n_stage ? (uint32_t)v.buf[pos] : (uint32_t)__ldg(v.gtext + pos);
+__device__ __forceinline__ uint32_t tbyte(const TextView &v, uint32_t pos) {
+    if (pos < v.n_stage) return v.buf[pos];
+    uint32_t r = 0;
+    GLOP_CK(v.hdr, pos < v.avail, 20, pos) r = __ldg(v.gtext + pos);
+    return r;
 }
 
-// 4 text bytes starting at pos (little-endian); bytes past the staged region
-// come from global memory one by one (patterns longer than the halo)
-__device__ __forceinline__ uint32_t tile_word(const TileView &v, uint32_t pos, uint32_t end) {
-    if (pos + 8 <= v.n_stage) {
-        const uint32_t *b32 = (const uint32_t *)v.buf;
-        uint32_t a = pos >> 2;
-        return __funnelshift_r(b32[a], b32[a + 1], 8 * (pos & 3));
-    }
-    uint32_t w = 0;
-    for (uint32_t k = 0; k < 4 && pos + k < end; ++k) w |= tile_byte(v, pos + k) << (8 * k);
-    return w;
+// 4 text bytes at pos (aligned shared-memory words and a funnel shift)
+__device__ __forceinline__ uint32_t tword(const uint32_t *b32, uint32_t pos) {
+    const uint32_t a = pos >> 2;
+    return __funnelshift_r(b32[a], b32[a + 1], 8 * (pos & 3));
 }
 
-// 4 chain bytes starting at chain_bytes[o] (the array is padded by 8 zero bytes)
-__device__ __forceinline__ uint32_t chain_word(const uint8_t *cb, uint32_t o) {
-    const uint32_t *c32 = (const uint32_t *)cb;
-    uint32_t a = o >> 2;
-    return __funnelshift_r(__ldg(c32 + a), __ldg(c32 + a + 1), 8 * (o & 3));
-}
-
-// Deepest terminal state reached from state s, next text byte at tile position
-// pos, walk bounded by end (segment end / text end, tile relative).
-__device__ uint32_t walk(const GlopDevAutomaton &A, const uint8_t *cls_s, const int32_t *rows_s, uint32_t hot_n,
-                         const TileView &v, uint32_t s, uint32_t pos, uint32_t end, uint32_t t) {
+template <bool ROW16>
+__device__ __forceinline__ uint32_t row_entry(const GlopDevAutomaton &A, const void *rows_s, uint32_t hot_n,
+                                              uint32_t s, uint32_t cl, uint32_t *hdr) {
     const uint32_t C = A.n_classes;
+    (void)hdr;
+    GLOP_BAIL(hdr, s < A.n_dense && cl < C, 21, s, 0u)
+    const uint32_t r = s - A.hot_lo;
+    if (ROW16) {
+        const uint32_t e = (r < hot_n)
+                               ? (uint32_t)reinterpret_cast<const uint16_t *>(rows_s)[r * C + cl]
+                               : (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(A.rows) + (size_t)s * C + cl);
+        return (e & 0x7FFFu) | ((e & 0x8000u) << 16);
+    }
+    return (r < hot_n) ? (uint32_t)reinterpret_cast<const int32_t *>(rows_s)[r * C + cl]
+                       : (uint32_t)__ldg(reinterpret_cast<const int32_t *>(A.rows) + (size_t)s * C + cl);
+}
+
+// Deepest terminal state reached from state s with the next text byte at
+// sub-tile position pos; the walk never reads at or past end.
+template <bool ROW16>
+__device__ uint32_t walk(const GlopDevAutomaton &A, const uint8_t *cls_s, const void *rows_s, uint32_t hot_n,
+                         const TextView &v, uint32_t s, uint32_t pos, uint32_t end, uint32_t t, uint32_t *hdr) {
+    const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf);
     while (true) {
+        if (s >= A.n_states) { fail_check(hdr, 1, s); return 0u; }
         if (s < A.n_dense) {
             if (pos >= end) return t;
-            uint32_t cl = cls_s[tile_byte(v, pos)];
-            uint32_t r = s - A.hot_lo;
-            int32_t e = (r < hot_n) ? rows_s[r * C + cl] : __ldg(A.rows + (size_t)s * C + cl);
+            const uint32_t e = row_entry<ROW16>(A, rows_s, hot_n, s, cls_s[tbyte(v, pos)], hdr);
             if (!e) return t;
-            s = (uint32_t)e & GLOP_STATE_MASK;
+            s = e & GLOP_STATE_MASK;
             ++pos;
-            if ((uint32_t)e & GLOP_TERM) t = s;
+            if (e & GLOP_TERM) t = s;
         } else {
-            const uint4 ch = __ldg(reinterpret_cast<const uint4 *>(A.chain) + (s - A.n_dense));
-            const uint32_t off = ch.x, rem = ch.y, exitv = ch.z;
+            const uint4 *rec = reinterpret_cast<const uint4 *>(A.chain) + 2 * (size_t)(s - A.n_dense);
+            const uint4 c0 = __ldg(rec), c1 = __ldg(rec + 1);
+            const uint32_t exitv = c1.x, term = c1.y, tm = c1.z & 0xFFFFu, rem = (c1.z >> 16) & 0xFFu,
+                           nst = c1.z >> 24;
             const uint32_t lim = min(rem, end - pos);
-            uint32_t m = 0;
-            while (m < lim) {
-                uint32_t x = tile_word(v, pos + m, end) ^ chain_word(A.chain_bytes, off + m);
-                if (x) { m += (uint32_t)(__ffs(x) - 1) >> 3; break; }
-                m += 4;
+            uint32_t m;
+            if (pos + 20 <= v.n_stage) {
+                const uint32_t x0 = tword(b32, pos) ^ c0.x, x1 = tword(b32, pos + 4) ^ c0.y,
+                               x2 = tword(b32, pos + 8) ^ c0.z, x3 = tword(b32, pos + 12) ^ c0.w;
+                m = x0   ? (uint32_t)(__ffs(x0) - 1) >> 3
+                    : x1 ? 4 + ((uint32_t)(__ffs(x1) - 1) >> 3)
+                    : x2 ? 8 + ((uint32_t)(__ffs(x2) - 1) >> 3)
+                    : x3 ? 12 + ((uint32_t)(__ffs(x3) - 1) >> 3)
+                         : 16u;
+                m = min(m, lim);
+            } else {
+                m = 0;
+                while (m < lim) {
+                    const uint32_t w = m < 4 ? c0.x : m < 8 ? c0.y : m < 12 ? c0.z : c0.w;
+                    if (tbyte(v, pos + m) != ((w >> (8 * (m & 3))) & 0xFFu)) break;
+                    ++m;
+                }
             }
-            m = min(m, lim);
-            const uint32_t nchain = rem - (exitv ? 1u : 0u);
+            const uint32_t r = min(m, nst);
+            const uint32_t hit = tm & ((2u << r) - 1u);
+            if (hit) t = s + 31 - __clz(hit);
+            else if (term) t = term;
             if (exitv && m == rem) {
-                uint32_t tt = __ldg(&A.chain[s + nchain - A.n_dense].term);
-                if (tt) t = tt;
                 s = exitv & GLOP_STATE_MASK;
-                if (exitv & GLOP_TERM) t = s;
                 pos += m;
+                if (exitv & GLOP_TERM) t = s;
                 continue;
             }
-            uint32_t tt = __ldg(&A.chain[s + min(m, nchain) - A.n_dense].term);
-            return tt ? tt : t;
+            return t;
         }
     }
-}
-
-// ---------------------------------------------------------------- look-back
-// Exclusive prefix of tile k's match count over all earlier tiles (decoupled
-// look-back over tile order; tiles are claimed in increasing order so every
-// predecessor is owned by a running group).  Called by one full warp.
-__device__ unsigned long long lookback(unsigned long long *tstat, uint64_t k, unsigned long long agg, int lane,
-                                       long long budget, uint32_t *hdr) {
-    if (k == 0) {
-        if (lane == 0) st_relaxed(&tstat[0], FLAG_PRE | agg);
-        return 0;
-    }
-    if (lane == 0) st_relaxed(&tstat[k], FLAG_AGG | agg);
-    unsigned long long excl = 0;
-    long long j = (long long)k - 1;
-    bool timed_out = false;
-    while (true) {
-        long long idx = j - lane;
-        unsigned long long v = FLAG_PRE;  // before tile 0: prefix 0
-        if (idx >= 0) {
-            long long t0 = clock64();
-            while (true) {
-                v = ld_relaxed(&tstat[idx]);
-                if (v >> 62) break;
-                if (clock64() - t0 > budget) { timed_out = true; v = FLAG_PRE; break; }
-            }
-        }
-        unsigned pm = __ballot_sync(FULL, (v >> 62) == 2ull);
-        int last = pm ? __ffs(pm) - 1 : 31;
-        unsigned long long val = (lane <= last) ? (v & VAL_MASK) : 0ull;
-        for (int d = 16; d; d >>= 1) val += shfl_xor64(val, d);
-        excl += val;
-        if (pm) break;
-        j -= 32;
-    }
-    if (__any_sync(FULL, timed_out) && lane == 0) atomicOr(hdr, WS_TIMEOUT);
-    if (lane == 0) st_relaxed(&tstat[k], FLAG_PRE | (excl + agg));
-    return excl;
 }
 
 // ---------------------------------------------------------------- kernels
-// Zero the tile status words and the header; for batches, check the segment
-// table and find the first segment of every tile.
-__global__ void init_kernel(uint32_t *hdr, unsigned long long *tstat, uint32_t *tile_seg, uint64_t n_tiles,
-                            const uint64_t *seg, uint32_t n_seg, uint64_t len, unsigned long long *d_count,
-                            int zero_header) {
-    uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+// Zero the workspace header; for batches also check the segment table and
+// find, for every sub-tile, the last segment starting at or before it.
+__global__ void init_kernel(uint32_t *hdr, uint32_t *tile_seg, uint64_t n_sub, const uint64_t *seg, uint32_t n_seg,
+                            uint64_t len, unsigned long long *d_count, int zero_header, int nothing) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     if (zero_header && tid < kHeaderBytes / 4) hdr[tid] = 0;
-    for (uint64_t k = tid; k < n_tiles; k += nthr) tstat[k] = 0ull;
-    if (n_tiles == 0 && tid == 0) *d_count = 0ull;
+    if (nothing && tid == 0) *d_count = 0ull;
     if (!seg) return;
     bool bad = false;
     for (uint64_t s = tid; s < n_seg; s += nthr) {
-        uint64_t a = seg[s], b = seg[s + 1];
+        const uint64_t a = seg[s], b = seg[s + 1];
         if (b < a || b - a > 0xFFFFFFFFull || b > len) bad = true;
     }
     if (bad) {
         atomicOr(hdr, WS_EINVAL);
         *d_count = 0ull;
     }
-    // tile_seg[k] = last segment whose start <= k * TILE (0 if none), k in [0, n_tiles]
-    for (uint64_t k = tid; k <= n_tiles; k += nthr) {
-        uint64_t x = k * TILE;
-        uint32_t lo = 0, hi = n_seg;  // answer in [lo, hi]
+    for (uint64_t k = tid; k <= n_sub; k += nthr) {
+        const uint64_t x = k * SUB;
+        uint32_t lo = 0, hi = n_seg;
         while (lo < hi) {
-            uint32_t mid = (lo + hi + 1) >> 1;
+            const uint32_t mid = (lo + hi + 1) >> 1;
             if (seg[mid] <= x) lo = mid; else hi = mid - 1;
         }
         tile_seg[k] = lo;
     }
 }
 
-template <int FILT, bool BATCH>
-__global__ void __launch_bounds__(1024, 1) scan_kernel(const KParams p) {
+template <int FILT, bool BATCH, bool ROW16>
+__global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const GlopDevAutomaton &A = p.A;
-    const uint32_t tid = threadIdx.x, nthr = blockDim.x;
-    if (BATCH && (ld_relaxed32(p.hdr) & WS_EINVAL)) return;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (BATCH && (ld_acquire32(p.hdr) & WS_EINVAL)) return;
 
-    // ---- stage the shared tables (class map, start filter, gram table, hot rows) ----
     uint8_t *cls_s = smem;
     uint32_t *fb_s = reinterpret_cast<uint32_t *>(smem + 256);
-    uint32_t *bm_s = reinterpret_cast<uint32_t *>(smem + p.off_bitmap);
-    GlopGramSlot *gr_s = reinterpret_cast<GlopGramSlot *>(smem + p.off_grams);
-    int32_t *rows_s = reinterpret_cast<int32_t *>(smem + p.off_rows);
+    const uint32_t *bm_s = reinterpret_cast<const uint32_t *>(smem + p.off_bitmap);
+    const GlopGramSlot *grams =
+        p.grams_in_smem ? reinterpret_cast<const GlopGramSlot *>(smem + p.off_grams) : A.grams;
+    const void *rows_s =
+        smem + p.off_rows + (((size_t)A.hot_lo * A.n_classes * (ROW16 ? 2u : 4u)) & 15);
+    CtaMisc *mc = reinterpret_cast<CtaMisc *>(smem + p.off_misc);
+    uint8_t *ring = smem + p.off_ring;
+
+    // ---- stage the tables: class map, start filter, gram table, hot rows ----
     {
         if (tid < 64) reinterpret_cast<uint32_t *>(cls_s)[tid] = __ldg(reinterpret_cast<const uint32_t *>(A.cls) + tid);
         if (tid < 8) fb_s[tid] = 0;
         if (FILT) {
             const uint4 *src = reinterpret_cast<const uint4 *>(A.bitmap);
-            uint4 *dst = reinterpret_cast<uint4 *>(bm_s);
-            for (uint32_t i = tid; i < (1u << A.bm_log2) / 128; i += nthr) dst[i] = __ldg(src + i);
+            uint4 *dst = reinterpret_cast<uint4 *>(smem + p.off_bitmap);
+            for (uint32_t i = tid; i < (1u << A.bm_log2) / 128; i += THREADS) dst[i] = __ldg(src + i);
             if (p.grams_in_smem) {
                 const uint4 *gs = reinterpret_cast<const uint4 *>(A.grams);
-                uint4 *gd = reinterpret_cast<uint4 *>(gr_s);
-                for (uint32_t i = tid; i < (1u << A.ht_log2); i += nthr) gd[i] = __ldg(gs + i);
+                uint4 *gd = reinterpret_cast<uint4 *>(smem + p.off_grams);
+                for (uint32_t i = tid; i < (1u << A.ht_log2); i += THREADS) gd[i] = __ldg(gs + i);
             }
         }
-        const uint32_t nrow = p.hot_n * A.n_classes;
-        const int32_t *rsrc = A.rows + (size_t)A.hot_lo * A.n_classes;
-        for (uint32_t i = tid; i < nrow; i += nthr) rows_s[i] = __ldg(rsrc + i);
+        // hot rows: copied in 16-byte units from the 16-byte boundary at or before their start
+        const uint32_t esz = ROW16 ? 2u : 4u;
+        const size_t start = (size_t)A.hot_lo * A.n_classes * esz;
+        const uint32_t lead = (uint32_t)(start & 15);
+        const uint32_t n16 = (lead + p.hot_n * A.n_classes * esz + 15) / 16;
+        const uint4 *rsrc = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(A.rows) + start - lead);
+        uint4 *rdst = reinterpret_cast<uint4 *>(smem + p.off_rows);
+        for (uint32_t i = tid; i < n16; i += THREADS) rdst[i] = __ldg(rsrc + i);
+        if (tid == 0) {
+            for (uint32_t s = 0; s < NSTAGE; ++s) {
+                mbar_init(&mc->full[s], 1);
+                mbar_init(&mc->empty[s], NCONS);
+            }
+            mc->rec_cursor = 0;
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
     }
     __syncthreads();
     if (!FILT) {
-        // bytes that start some pattern: the initial state has a transition on them
         if (tid < 256) {
-            uint32_t e = (uint32_t)__ldg(A.rows + cls_s[tid]);
+            const uint32_t e = ROW16 ? (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(A.rows) + cls_s[tid])
+                                     : (uint32_t)__ldg(reinterpret_cast<const int32_t *>(A.rows) + cls_s[tid]);
             if (e) atomicOr(&fb_s[tid >> 5], 1u << (tid & 31));
         }
         __syncthreads();
     }
-    const GlopGramSlot *grams = p.grams_in_smem ? gr_s : A.grams;
-
-    // ---- group setup ----
-    const uint32_t gid = tid / GT, gtid = tid % GT, lane = tid & 31, warp_g = gtid >> 5;
-    const uint32_t bar_id = gid + 1;
-    uint8_t *G = smem + p.off_groups + gid * p.group_bytes;
-    uint32_t *res = reinterpret_cast<uint32_t *>(G + 2 * p.tbuf);
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(res + TILE);
-    unsigned long long *wsum = cnt + GT;
-    unsigned long long *segl = wsum + WARPS_G;
-    GroupMisc *gm = reinterpret_cast<GroupMisc *>(segl + SEGCAP + 1);
-
-    auto issue = [&](uint64_t k, int bb) {
-        uint64_t s0 = k * TILE;
-        uint64_t n_stage = min((uint64_t)(TILE + p.halo), p.len - s0);
-        uint32_t bytes = p.aligned ? (uint32_t)(n_stage & ~15ull) : 0u;
-        tma_load(G + bb * p.tbuf, p.text + s0, bytes, &gm->mbar[bb]);
-    };
-
-    if (gtid == 0) {
-        mbar_init(&gm->mbar[0], 1);
-        mbar_init(&gm->mbar[1], 1);
-        fence_barrier_init();
-        gm->abort = 0;
-        unsigned long long k0 = atomicAdd(reinterpret_cast<unsigned long long *>(p.hdr + 2), 1ull);
-        gm->tick[0] = k0;
-        if (k0 < p.n_tiles) issue(k0, 0);
-    }
-    group_bar(bar_id);
 
     const uint32_t g = A.gram_len;
     const uint32_t w1mask = FILT == 8 ? glop_w1_mask(g) : 0u;
     const uint32_t bsh = 32u - A.bm_log2;
     const uint32_t htmask = (1u << A.ht_log2) - 1u;
-    uint32_t phase = 0;
-    int b = 0;
-    bool pending_other = false;
-    while (true) {
-        const uint64_t k = gm->tick[b];
-        if (k >= p.n_tiles) break;
-        if (gtid == 0) {
-            unsigned long long k1 = atomicAdd(reinterpret_cast<unsigned long long *>(p.hdr + 2), 1ull);
-            gm->tick[b ^ 1] = k1;
-            if (k1 < p.n_tiles) issue(k1, b ^ 1);
-        }
-        pending_other = true;
-        const uint64_t s0 = k * TILE;
-        const uint32_t n_stage = (uint32_t)min((uint64_t)(TILE + p.halo), p.len - s0);
-        const uint32_t tile_len = min(TILE, n_stage);
-        uint8_t *buf = G + b * p.tbuf;
-        // bytes the bulk copy does not cover (unaligned tail, or everything when the text is unaligned)
-        {
-            uint32_t done = p.aligned ? (n_stage & ~15u) : 0u;
-            for (uint32_t y = done + gtid; y < n_stage; y += GT) buf[y] = __ldg(p.text + s0 + y);
-        }
-        if (!mbar_wait(&gm->mbar[b], (phase >> b) & 1u, p.spin_budget)) {
-            atomicOr(p.hdr, WS_TIMEOUT);
-            gm->abort = 1;
-        }
-        phase ^= 1u << b;
-        if (BATCH && gtid == 0) {
-            uint32_t a = __ldg(p.tile_seg + k), e = __ldg(p.tile_seg + k + 1) + 1;
-            if (e > p.n_seg) e = p.n_seg;
-            uint32_t L = e - a;
-            gm->seg_a = a;
-            gm->seg_L = L;
-            gm->seg_fallback = L > SEGCAP;
-            if (L <= SEGCAP)
-                for (uint32_t x = 0; x <= L; ++x) segl[x] = __ldg((const unsigned long long *)p.seg + a + x);
-        }
-        group_bar(bar_id);
-        if (gm->abort) break;
+    constexpr uint32_t REC_W = BATCH ? 3u : 2u;  // record size in uint32
 
-        // segment of an absolute offset: (index, start, end); false outside every segment
-        auto seg_of = [&](uint64_t iabs, uint32_t &si, uint64_t &sstart, uint64_t &send) -> bool {
-            if (!BATCH) { si = 0; sstart = 0; send = p.len; return true; }
-            const uint32_t a = gm->seg_a, L = gm->seg_L;
-            uint32_t kk;
-            if (!gm->seg_fallback) {
-                if (segl[0] > iabs) return false;
-                kk = seg_find_smem(segl, L, iabs);
-                if (kk >= L) return false;
-                sstart = segl[kk];
-                send = segl[kk + 1];
+    // walk from sub-tile offset off (the text ends for this walk at endr)
+    auto walk_at = [&](const TextView &v, uint32_t off, uint32_t endr) -> uint32_t {
+        if (FILT) {
+            if (off + g > endr) return 0u;
+            uint32_t w0 = 0, w1 = 0;
+            if (off + 12 <= v.n_stage) {
+                const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf);
+                const uint32_t a = off >> 2, sh = 8 * (off & 3);
+                const uint32_t y1 = b32[a + 1];
+                w0 = __funnelshift_r(b32[a], y1, sh);
+                if (FILT == 8) w1 = __funnelshift_r(y1, b32[a + 2], sh) & w1mask;
             } else {
-                if (__ldg((const unsigned long long *)p.seg + a) > iabs) return false;
-                kk = seg_find_global(p.seg, a, a + L, iabs) - a;
-                if (kk >= L) return false;
-                sstart = __ldg((const unsigned long long *)p.seg + a + kk);
-                send = __ldg((const unsigned long long *)p.seg + a + kk + 1);
+                for (uint32_t k = 0; k < 4; ++k) w0 |= tbyte(v, off + k) << (8 * k);
+                if (FILT == 8)
+                    for (uint32_t k = 4; k < g; ++k) w1 |= tbyte(v, off + k) << (8 * (k - 4));
             }
-            si = a + kk;
-            return iabs < send;
-        };
+            uint32_t h = w0 * GLOP_HASH_M0;
+            if (FILT == 8) h ^= w1 * GLOP_HASH_M1;
+            uint32_t slot = glop_table_slot(h, A.ht_log2), val = 0;
+            while (true) {
+                const uint4 e = *reinterpret_cast<const uint4 *>(grams + slot);
+                if (!e.z) break;
+                if (e.x == w0 && e.y == w1) { val = e.z; break; }
+                slot = (slot + 1) & htmask;
+            }
+            if (!val) return 0u;
+            const uint32_t s = val & GLOP_STATE_MASK;
+            return walk<ROW16>(A, cls_s, rows_s, p.hot_n, v, s, off + g, endr, (val & GLOP_TERM) ? s : 0u, p.hdr);
+        }
+        return walk<ROW16>(A, cls_s, rows_s, p.hot_n, v, 0u, off, endr, 0u, p.hdr);
+    };
 
-        // ---- 2. start filter over 16 consecutive offsets ----
+    // start filter: bit j of the result = offset 32*lane + j of the sub-tile may start a match
+    auto filter = [&](const TextView &v, uint32_t sub_len, uint64_t avail) -> uint32_t {
+        uint32_t x[10];
+        const uint32_t o = 32 * lane;
+        if (v.n_stage >= SUB + 16) {
+            const uint4 v0 = *reinterpret_cast<const uint4 *>(v.buf + o);
+            const uint4 v1 = *reinterpret_cast<const uint4 *>(v.buf + o + 16);
+            const uint2 v2 = *reinterpret_cast<const uint2 *>(v.buf + o + 32);
+            x[0] = v0.x; x[1] = v0.y; x[2] = v0.z; x[3] = v0.w;
+            x[4] = v1.x; x[5] = v1.y; x[6] = v1.z; x[7] = v1.w;
+            x[8] = v2.x; x[9] = v2.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 10; ++k) {
+                uint32_t w = 0;
+                for (uint32_t b = 0; b < 4; ++b) {
+                    const uint32_t pos = o + 4 * k + b;
+                    if (pos < avail) w |= tbyte(v, pos) << (8 * b);
+                }
+                x[k] = w;
+            }
+        }
         uint32_t mask = 0;
-        {
-            const uint4 *b4 = reinterpret_cast<const uint4 *>(buf);
-            const uint4 v0 = b4[gtid], v1 = b4[gtid + 1];
-            const uint32_t x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-            for (int j = 0; j < (int)KOFF; ++j) {
-                uint32_t bit;
-                if (FILT) {
-                    uint32_t w0 = __funnelshift_r(x[j >> 2], x[(j >> 2) + 1], 8 * (j & 3));
-                    uint32_t h = w0 * GLOP_HASH_M0;
-                    if (FILT == 8) {
-                        uint32_t w1 = __funnelshift_r(x[(j >> 2) + 1], x[(j >> 2) + 2], 8 * (j & 3)) & w1mask;
-                        h ^= w1 * GLOP_HASH_M1;
-                    }
-                    uint32_t bi = h >> bsh;
-                    bit = (bm_s[bi >> 5] >> (bi & 31)) & 1u;
-                } else {
-                    uint32_t by = (x[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-                    bit = (fb_s[by >> 5] >> (by & 31)) & 1u;
-                }
-                mask |= bit << j;
+        for (int j = 0; j < 32; ++j) {
+            uint32_t bit;
+            if (FILT) {
+                uint32_t h = __funnelshift_r(x[j >> 2], x[(j >> 2) + 1], 8 * (j & 3)) * GLOP_HASH_M0;
+                if (FILT == 8)
+                    h ^= (__funnelshift_r(x[(j >> 2) + 1], x[(j >> 2) + 2], 8 * (j & 3)) & w1mask) * GLOP_HASH_M1;
+                const uint32_t bi = h >> bsh;
+                bit = (bm_s[bi >> 5] >> (bi & 31)) & 1u;
+            } else {
+                const uint32_t by = (x[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+                bit = (fb_s[by >> 5] >> (by & 31)) & 1u;
             }
-            const uint32_t first = gtid * KOFF;
-            if (first + KOFF > tile_len) mask &= (first >= tile_len) ? 0u : ((1u << (tile_len - first)) - 1u);
+            mask |= bit << j;
         }
+        if (o + 32 > sub_len) mask &= (o >= sub_len) ? 0u : ((1u << (sub_len - o)) - 1u);
+        return mask;
+    };
 
-        // ---- 3. per-warp queue of surviving offsets, in offset order ----
-        const uint32_t nsurv = __popc(mask);
-        uint32_t incl = nsurv;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t vv = __shfl_up_sync(FULL, incl, d);
-            if (lane >= (uint32_t)d) incl += vv;
-        }
-        const uint32_t qpos = incl - nsurv;
-        const uint32_t qtotal = __shfl_sync(FULL, incl, 31);
-        uint32_t *q = res + warp_g * (32 * KOFF);
-        {
-            uint32_t m = mask, at = qpos;
-            while (m) {
-                int bb = __ffs(m) - 1;
-                m &= m - 1;
-                q[at++] = gtid * KOFF + bb;
+    // segment holding absolute offset iabs (list of warp slot cw): false outside every segment
+    auto seg_of = [&](uint32_t cw, bool onchip, uint64_t iabs, uint32_t &si, uint64_t &sstart,
+                      uint64_t &send) -> bool {
+        const uint32_t a = mc->seg_a[cw], L = mc->seg_L[cw];
+        uint32_t lo = 0, hi = L;
+        if (onchip) {
+            const unsigned long long *e = mc->segl[cw];
+            if (e[0] > iabs) return false;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (e[mid] <= iabs) lo = mid; else hi = mid - 1;
             }
+            if (lo >= L) return false;
+            sstart = e[lo];
+            send = e[lo + 1];
+        } else {
+            const unsigned long long *e = reinterpret_cast<const unsigned long long *>(p.seg) + a;
+            GLOP_BAIL(p.hdr, (uint64_t)a + L <= p.n_seg, 24, a, false)
+            if (__ldg(e) > iabs) return false;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(e + mid) <= iabs) lo = mid; else hi = mid - 1;
+            }
+            if (lo >= L) return false;
+            sstart = __ldg(e + lo);
+            send = __ldg(e + lo + 1);
         }
-        cnt[gtid] = 0ull;
-        __syncwarp();
+        si = a + lo;
+        return iabs < send;
+    };
 
-        TileView view{buf, p.text + s0, n_stage};
-        for (uint32_t qi = lane; qi < qtotal; qi += 32) {
-            const uint32_t off = q[qi];
-            uint32_t tres = 0;
-            uint32_t si;
-            uint64_t sstart, send;
-            if (seg_of(s0 + off, si, sstart, send)) {
-                uint64_t endr64 = send - s0;
-                uint32_t endr = (uint32_t)min(endr64, (uint64_t)0xFFFFFFFFu);
-                if (FILT) {
-                    if (off + g <= endr) {
-                        const uint32_t *b32 = reinterpret_cast<const uint32_t *>(buf);
-                        const uint32_t a = off >> 2, sh = 8 * (off & 3);
-                        const uint32_t y0 = b32[a], y1 = b32[a + 1];
-                        const uint32_t w0 = __funnelshift_r(y0, y1, sh);
-                        uint32_t w1 = 0, h = w0 * GLOP_HASH_M0;
-                        if (FILT == 8) {
-                            w1 = __funnelshift_r(y1, b32[a + 2], sh) & w1mask;
-                            h ^= w1 * GLOP_HASH_M1;
-                        }
-                        uint32_t slot = glop_table_slot(h, A.ht_log2), val = 0;
-                        while (true) {
-                            const uint4 e = *reinterpret_cast<const uint4 *>(grams + slot);
-                            if (!e.z) break;
-                            if (e.x == w0 && e.y == w1) { val = e.z; break; }
-                            slot = (slot + 1) & htmask;
-                        }
-                        if (val) {
-                            uint32_t s = val & GLOP_STATE_MASK;
-                            tres = walk(A, cls_s, rows_s, p.hot_n, view, s, off + g, endr, (val & GLOP_TERM) ? s : 0u);
-                        }
-                    }
-                } else {
-                    tres = walk(A, cls_s, rows_s, p.hot_n, view, 0u, off, endr, 0u);
-                }
+    // the segment list of sub-tile j into warp slot cw (whole warp)
+    auto load_segs = [&](uint32_t cw, uint64_t j) -> bool {
+        if (lane == 0) {
+            uint32_t a = 0, e = 1;
+            GLOP_CK(p.hdr, j + 1 <= p.n_sub, 22, j) {
+                a = __ldg(p.tile_seg + j);
+                e = __ldg(p.tile_seg + j + 1) + 1;
             }
-            q[qi] = tres;
-            if (tres) {
-                unsigned long long c = __ldg(A.cum_off + tres + 1) - __ldg(A.cum_off + tres);
-                atomicAdd(&cnt[off / KOFF], c);
-            }
+            if (e > p.n_seg) e = p.n_seg;
+            mc->seg_a[cw] = a;
+            mc->seg_L[cw] = e - a;
         }
         __syncwarp();
+        const uint32_t L = mc->seg_L[cw], a = mc->seg_a[cw];
+        if (L <= SEGW)
+            for (uint32_t x = lane; x <= L; x += 32)
+                GLOP_CK(p.hdr, a + x <= p.n_seg && cw < 32, 23, a + x)
+                mc->segl[cw][x] = __ldg(reinterpret_cast<const unsigned long long *>(p.seg) + a + x);
+        __syncwarp();
+        return L <= SEGW;
+    };
 
-        // ---- 4. counts -> group scan -> look-back -> emit ----
-        const unsigned long long c = cnt[gtid];
-        unsigned long long cincl = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            unsigned long long vv = shfl_up64(cincl, d);
-            if (lane >= (uint32_t)d) cincl += vv;
+    // Expand up to 32 matching offsets held one per lane (state t, fields f0/f1)
+    // into output slots o, o+1, ...: all patterns of an offset, offsets in lane
+    // order.  Returns the number of outputs.
+    auto expand = [&](uint32_t t, uint32_t f0, uint32_t f1, unsigned long long o) -> uint32_t {
+        uint32_t lo = 0, c = 0;
+        if (t >= A.n_states) { if (t) fail_check(p.hdr, 2, t); t = 0; }
+        if (t) {
+            lo = __ldg(A.cum_off + t);
+            c = __ldg(A.cum_off + t + 1) - lo;
         }
-        if (lane == 31) wsum[warp_g] = cincl;
-        group_bar(bar_id);
-        unsigned long long wpre = 0, ttot = 0;
-#pragma unroll
-        for (uint32_t w = 0; w < WARPS_G; ++w) {
-            unsigned long long vv = wsum[w];
-            if (w < warp_g) wpre += vv;
-            ttot += vv;
-        }
-        if (warp_g == 0) {
-            unsigned long long ex = lookback(p.tstat, k, ttot, (int)lane, p.spin_budget, p.hdr);
-            if (lane == 0) {
-                gm->base = ex;
-                if (k == p.n_tiles - 1) {
-                    unsigned long long total = ex + ttot;
-                    *p.d_count = total;
-                    *reinterpret_cast<unsigned long long *>(p.hdr + 4) = total;
-                    if (total > p.cap) atomicOr(p.hdr, WS_OVERFLOW);
-                }
-            }
-        }
-        group_bar(bar_id);
-        if (c) {
-            unsigned long long o = gm->base + wpre + cincl - c;
-            uint32_t m = mask, r = 0;
-            while (m && o < p.cap) {
-                const int bb = __ffs(m) - 1;
-                m &= m - 1;
-                const uint32_t tv = q[qpos + r];
-                ++r;
-                if (!tv) continue;
-                const uint32_t lo = __ldg(A.cum_off + tv), hi = __ldg(A.cum_off + tv + 1);
-                const uint64_t iabs = s0 + gtid * KOFF + bb;
+        const uint32_t incl = warp_incl_scan(c, lane), excl = incl - c, tot = __shfl_sync(FULL, incl, 31);
+        for (uint32_t s0 = 0; s0 < tot; s0 += 32) {
+            const uint32_t slot = s0 + lane;
+            const uint32_t ow = owner_of(excl, slot);
+            const uint32_t lo_o = __shfl_sync(FULL, lo, ow), ex_o = __shfl_sync(FULL, excl, ow);
+            const uint32_t f0_o = __shfl_sync(FULL, f0, ow), f1_o = __shfl_sync(FULL, f1, ow);
+            const unsigned long long pos = o + slot;
+            if (slot < tot && pos < p.cap) {
+                uint32_t pid = 0;
+                GLOP_CK(p.hdr, lo_o + (slot - ex_o) < A.n_cum_ids, 25, lo_o) pid = __ldg(A.cum_ids + lo_o + (slot - ex_o));
                 if (BATCH) {
-                    uint32_t si = 0;
-                    uint64_t sstart = 0, send = 0;
-                    seg_of(iabs, si, sstart, send);
-                    uint32_t *ob = reinterpret_cast<uint32_t *>(p.out);
-                    for (uint32_t x = lo; x < hi && o < p.cap; ++x, ++o) {
-                        ob[3 * o] = si;
-                        ob[3 * o + 1] = (uint32_t)(iabs - sstart);
-                        ob[3 * o + 2] = __ldg(A.cum_ids + x);
-                    }
+                    uint32_t *ob = reinterpret_cast<uint32_t *>(p.out) + 3 * pos;
+                    __stcs(ob, f0_o);
+                    __stcs(ob + 1, f1_o);
+                    __stcs(ob + 2, pid);
                 } else {
-                    uint2 *ob = reinterpret_cast<uint2 *>(p.out);
-                    for (uint32_t x = lo; x < hi && o < p.cap; ++x, ++o)
-                        ob[o] = make_uint2((uint32_t)iabs, __ldg(A.cum_ids + x));
+                    __stcs(reinterpret_cast<uint2 *>(p.out) + pos, make_uint2(f0_o, pid));
                 }
             }
         }
-        b ^= 1;
-        pending_other = false;
+        return tot;
+    };
+
+    // Walk every survivor of sub-tile j.  Record mode: (offset, state) records
+    // into this block's scratch slice and a descriptor.  Direct mode (output
+    // position known): expand straight into the output.
+    auto process = [&](uint64_t j, const TextView &v, uint32_t cw, bool direct, unsigned long long obase) {
+        const uint64_t s0 = j * SUB;
+        const uint64_t avail = p.len - s0;
+        const uint32_t sub_len = (uint32_t)min((uint64_t)SUB, avail);
+        bool onchip = true;
+        if (BATCH) onchip = load_segs(cw, j);
+        const uint32_t mask = filter(v, sub_len, avail);
+        const uint32_t n = __popc(mask);
+        const uint32_t incl = warp_incl_scan(n, lane), excl = incl - n, total = __shfl_sync(FULL, incl, 31);
+        uint32_t rbase = 0;
+        bool ovf = false;
+        if (!direct) {
+            if (lane == 0) rbase = atomicAdd(&mc->rec_cursor, total);
+            rbase = __shfl_sync(FULL, rbase, 0);
+            ovf = (uint64_t)rbase + total > p.rec_cap_cta;
+        }
+        const uint32_t rabs = blockIdx.x * p.rec_cap_cta + rbase;
+        uint32_t *recs = p.records + (size_t)rabs * REC_W;
+        uint32_t nrec = 0;
+        unsigned long long nmatch = 0, o = obase;
+        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+            const uint32_t i = r0 + lane;
+            const uint32_t ow = owner_of(excl, i);
+            const uint32_t m_o = __shfl_sync(FULL, mask, ow), e_o = __shfl_sync(FULL, excl, ow);
+            uint32_t t = 0, f0 = 0, f1 = 0;
+            if (i < total) {
+                uint32_t off = ow * 32 + __fns(m_o, 0, (int)(i - e_o + 1));
+                if (off >= SUB) { fail_check(p.hdr, 3, off); off = 0; }
+                const uint64_t iabs = s0 + off;
+                uint32_t si = 0;
+                uint64_t sstart = 0, send = p.len;
+                bool in = true;
+                if (BATCH) in = seg_of(cw, onchip, iabs, si, sstart, send);
+                if (in) t = walk_at(v, off, (uint32_t)min(send - s0, (uint64_t)0xFFFFFFFFu));
+                if (BATCH) {
+                    f0 = si;
+                    f1 = (uint32_t)(iabs - sstart);
+                } else {
+                    f0 = (uint32_t)iabs;
+                }
+            }
+            if (direct) {
+                o += expand(t, f0, f1, o);
+            } else {
+                const uint32_t b = __ballot_sync(FULL, t != 0);
+                if (t) {
+                    const uint32_t pos = nrec + __popc(b & ((1u << lane) - 1u));
+                    GLOP_CK(p.hdr, t < A.n_states, 26, t) nmatch += __ldg(A.cum_off + t + 1) - __ldg(A.cum_off + t);
+                    GLOP_CK(p.hdr, ovf || (uint64_t)rabs + pos < p.rec_slots, 27, rabs + pos)
+                    if (!ovf) {
+                        uint32_t *rp = recs + (size_t)pos * REC_W;
+                        rp[0] = f0;
+                        if (BATCH) { rp[1] = f1; rp[2] = t; } else { rp[1] = t; }
+                    }
+                }
+                nrec += __popc(b);
+            }
+        }
+        if (!direct) {
+            nmatch = warp_sum64(nmatch);
+            if (lane == 0) {
+                SubDesc d;
+                d.rec_start = rabs;
+                d.n_rec = ovf ? REC_OVERFLOW : nrec;
+                d.n_match = nmatch;
+                GLOP_CK(p.hdr, j < p.n_sub, 28, j) p.desc[j] = d;
+                if (ovf) atomicAdd(p.hdr + 10, 1u);
+            }
+        }
+    };
+
+    // ================= phase A =================
+    if (warp == 0) {
+        // producer: chunk tickets -> ring slots
+        for (uint32_t cs = 0;; ++cs) {
+            const uint32_t slot = cs % NSTAGE;
+            if (cs >= NSTAGE) {
+                uint32_t ok = 1;
+                if (lane == 0) ok = mbar_wait(&mc->empty[slot], ((cs / NSTAGE) - 1) & 1u, p.spin_budget) ? 1u : 0u;
+                ok = __shfl_sync(FULL, ok, 0);
+                if (!ok) {
+                    if (lane == 0) atomicOr(p.hdr, WS_TIMEOUT);
+                    break;
+                }
+            }
+            unsigned long long k = 0;
+            if (lane == 0) k = atomicAdd(reinterpret_cast<unsigned long long *>(p.hdr + 2), 1ull);
+            k = shfl64(k, 0);
+            uint8_t *dst = ring + (size_t)slot * p.slot_bytes;
+            if (k >= p.n_chunks) {
+                if (lane == 0) {
+                    mc->slot_tile[slot] = END_TICKET;
+                    mbar_arrive(&mc->full[slot]);
+                }
+                break;
+            }
+            const uint64_t c0 = k * CHUNK;
+            const uint32_t n_stage = (uint32_t)min((uint64_t)(CHUNK + p.halo), p.len - c0);
+            const uint32_t bulk = p.aligned ? (n_stage & ~15u) : 0u;
+            for (uint32_t y = bulk + lane; y < n_stage; y += 32)
+                GLOP_CK(p.hdr, c0 + y < p.len && y < p.slot_bytes, 29, y) dst[y] = __ldg(p.text + c0 + y);
+            __syncwarp();
+            if (lane == 0) {
+                mc->slot_tile[slot] = k;
+                mc->slot_nstage[slot] = n_stage;
+                bool tma_ok = true;
+                GLOP_CK(p.hdr, c0 + bulk <= p.len && bulk <= p.slot_bytes && !(reinterpret_cast<uintptr_t>(p.text + c0) & 15) &&
+                                   !(smem_addr(dst) & 15) && (bulk & 15) == 0, 30, bulk) {}
+#ifdef GLOP_BOUNDS_CHECK
+                tma_ok = c0 + bulk <= p.len && bulk <= p.slot_bytes && !(reinterpret_cast<uintptr_t>(p.text + c0) & 15) &&
+                         !(smem_addr(dst) & 15) && (bulk & 15) == 0;
+#endif
+                if (bulk && tma_ok) tma_load(dst, p.text + c0, bulk, &mc->full[slot]);
+                else mbar_arrive(&mc->full[slot]);
+            }
+        }
+    } else {
+        const uint32_t cw = warp - 1;
+        for (uint32_t cs = 0;; ++cs) {
+            const uint32_t slot = cs % NSTAGE;
+            if (!mbar_wait(&mc->full[slot], (cs / NSTAGE) & 1u, p.spin_budget)) {
+                if (lane == 0) atomicOr(p.hdr, WS_TIMEOUT);
+                break;
+            }
+            const unsigned long long k = mc->slot_tile[slot];
+            if (k == END_TICKET) break;
+            const uint64_t j = k * NCONS + cw;
+            if (j < p.n_sub) {
+                const uint32_t ns = mc->slot_nstage[slot];
+                TextView v;
+                v.buf = ring + (size_t)slot * p.slot_bytes + cw * SUB;
+                v.gtext = p.text + j * SUB;
+                v.n_stage = ns > cw * SUB ? ns - cw * SUB : 0u;
+#ifdef GLOP_BOUNDS_CHECK
+                v.avail = p.len - j * SUB;
+                v.hdr = p.hdr;
+#endif
+                process(j, v, cw, false, 0ull);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&mc->empty[slot]);
+        }
     }
-    // a bulk copy still in flight into the other buffer (only after an abort): wait for it, bounded
-    if (pending_other && gtid == 0 && gm->tick[b ^ 1] < p.n_tiles)
-        mbar_wait(&gm->mbar[b ^ 1], (phase >> (b ^ 1)) & 1u, p.spin_budget);
+
+    // ================= phase B =================
+    const uint32_t G = gridDim.x;
+    grid_sync(p.hdr + 8, G, p.spin_budget, p.hdr);
+    const uint64_t R = (p.n_sub + G - 1) / G;
+    const uint64_t ra = min(p.n_sub, (uint64_t)blockIdx.x * R), rb = min(p.n_sub, ra + R);
+    {
+        unsigned long long sum = 0;
+        for (uint64_t j = ra + tid; j < rb; j += THREADS)
+            GLOP_CK(p.hdr, j < p.n_sub, 31, j) sum += __ldcg(&p.desc[j].n_match);
+        sum = warp_sum64(sum);
+        if (lane == 0) mc->red[warp] = sum;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long v = warp_sum64(mc->red[lane]);
+            if (lane == 0) p.sums[blockIdx.x] = v;
+        }
+    }
+    grid_sync(p.hdr + 9, G, p.spin_budget, p.hdr);
+    if (warp == 0) {
+        unsigned long long before = 0, all = 0;
+        for (uint32_t c = lane; c < G; c += 32) {
+            const unsigned long long v = __ldcg(p.sums + c);
+            if (c < blockIdx.x) before += v;
+            all += v;
+        }
+        before = warp_sum64(before);
+        all = warp_sum64(all);
+        if (lane == 0) {
+            mc->red[0] = before;
+            if (blockIdx.x == 0) {
+                *p.d_count = all;
+                *reinterpret_cast<unsigned long long *>(p.hdr + 4) = all;
+                if (all > p.cap) atomicOr(p.hdr, WS_OVERFLOW);
+            }
+        }
+    }
+    __syncthreads();
+    unsigned long long running = mc->red[0];
+    __syncthreads();
+
+    unsigned long long *bases = reinterpret_cast<unsigned long long *>(ring);  // the ring is free now
+    for (uint64_t p0 = ra; p0 < rb; p0 += PB) {
+        const uint32_t np = (uint32_t)min((uint64_t)PB, rb - p0);
+        // exclusive scan of the piece's match counts, 4 per thread
+        unsigned long long v[4], s = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t idx = tid * 4 + q;
+            v[q] = idx < np ? __ldcg(&p.desc[p0 + idx].n_match) : 0ull;
+            s += v[q];
+        }
+        unsigned long long inc = s;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long u = shfl_up64(inc, d);
+            if (lane >= (uint32_t)d) inc += u;
+        }
+        if (lane == 31) mc->red[warp] = inc;
+        __syncthreads();
+        unsigned long long wpre = 0, ptot = 0;
+        for (uint32_t w = 0; w < 32; ++w) {
+            const unsigned long long x = mc->red[w];
+            if (w < warp) wpre += x;
+            ptot += x;
+        }
+        unsigned long long e = running + wpre + inc - s;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t idx = tid * 4 + q;
+            if (idx < np) bases[idx] = e;
+            e += v[q];
+        }
+        __syncthreads();
+        for (uint32_t x = warp; x < np; x += 32) {
+            const uint64_t j = p0 + x;
+            uint4 dr = make_uint4(0, 0, 0, 0);
+            GLOP_CK(p.hdr, j < p.n_sub, 32, j) dr = __ldcg(reinterpret_cast<const uint4 *>(p.desc + j));
+            unsigned long long o = bases[x];
+            if (dr.y != REC_OVERFLOW && (uint64_t)dr.x + dr.y > p.rec_slots) {
+                fail_check(p.hdr, 4, dr.x);
+            } else if (dr.y != REC_OVERFLOW) {
+                const uint32_t *recs = p.records + (size_t)dr.x * REC_W;
+                for (uint32_t r0 = 0; r0 < dr.y; r0 += 32) {
+                    const uint32_t r = r0 + lane;
+                    uint32_t t = 0, f0 = 0, f1 = 0;
+                    if (r < dr.y) {
+                        const uint32_t *rp = recs + (size_t)r * REC_W;
+                        f0 = __ldcg(rp);
+                        if (BATCH) { f1 = __ldcg(rp + 1); t = __ldcg(rp + 2); } else { t = __ldcg(rp + 1); }
+                    }
+                    o += expand(t, f0, f1, o);
+                }
+            } else {
+                // the records did not fit: walk the sub-tile again from global memory
+                TextView gv;
+                gv.buf = nullptr;
+                gv.gtext = p.text + j * SUB;
+                gv.n_stage = 0u;
+#ifdef GLOP_BOUNDS_CHECK
+                gv.avail = p.len - j * SUB;
+                gv.hdr = p.hdr;
+#endif
+                process(j, gv, warp, true, o);
+            }
+        }
+        running += ptot;
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- host side
 struct DevProps {
-    int sms = 0, smem_optin = 0;
+    int sms = 0, smem_optin = 0, coop = 0;
 };
 
 DevProps props_of(int dev) {
@@ -617,63 +835,81 @@ DevProps props_of(int dev) {
     if (!cache[dev].sms) {
         cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&cache[dev].smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&cache[dev].coop, cudaDevAttrCooperativeLaunch, dev);
     }
     return cache[dev];
 }
 
-template <int FILT, bool BATCH>
-int launch_t(const KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st) {
+template <int FILT, bool BATCH, bool ROW16>
+int launch_t(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st) {
     static std::mutex mu;
     static uint32_t set_for[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
+    auto fn = scan_kernel<FILT, BATCH, ROW16>;
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev >= 0 && dev < 64 && set_for[dev] < smem) {
-            if (cudaFuncSetAttribute(scan_kernel<FILT, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
                 return 4;
             set_for[dev] = smem;
         }
     }
-    scan_kernel<FILT, BATCH><<<grid, kp.ngroups * GT, smem, st>>>(kp);
-    return cudaGetLastError() == cudaSuccess ? 0 : 4;
+    void *args[] = {&kp};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(THREADS), args, smem, st);
+    return e == cudaSuccess ? 0 : 4;
 }
 
 uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
+struct WsLayout {
+    uint64_t desc, sums, tile_seg, records, total;
+    uint64_t rec_slots;
+};
+
+WsLayout layout_of(uint64_t len, bool batch) {
+    const uint64_t n_sub = (len + SUB - 1) / SUB;
+    WsLayout w;
+    w.desc = kHeaderBytes;
+    w.sums = w.desc + 16 * n_sub;
+    w.tile_seg = w.sums + 8ull * kMaxGrid;
+    uint64_t after = w.tile_seg + (batch ? 4 * (n_sub + 1) : 0);
+    w.records = (after + 255) / 256 * 256;
+    w.rec_slots = std::max<uint64_t>(len / 8, 4096);
+    const uint64_t rec_bytes = batch ? 12 : 8;
+    w.total = (w.records + w.rec_slots * rec_bytes + 255) / 256 * 256;
+    return w;
+}
+
 }  // namespace
 
-uint64_t workspace_bytes(uint64_t len, bool batch) {
-    uint64_t n_tiles = (len + TILE - 1) / TILE;
-    uint64_t b = kHeaderBytes + 8 * n_tiles;
-    if (batch) b += 4 * (n_tiles + 1);
-    return (b + 255) / 256 * 256;
-}
+uint64_t workspace_bytes(uint64_t len, bool batch) { return layout_of(len, batch).total; }
 
 int launch_scan(const ScanLaunch &L) {
     const GlopDevAutomaton &A = *L.A;
     const bool batch = L.seg != nullptr;
-    const uint64_t n_tiles = (L.len + TILE - 1) / TILE;
-    if (L.ws_bytes < workspace_bytes(L.len, batch)) return 2;
-    uint32_t *hdr = reinterpret_cast<uint32_t *>(L.ws);
-    unsigned long long *tstat = reinterpret_cast<unsigned long long *>(reinterpret_cast<uint8_t *>(L.ws) + kHeaderBytes);
-    uint32_t *tile_seg = reinterpret_cast<uint32_t *>(tstat + n_tiles);
-    const bool nothing = (A.n_patterns == 0) || n_tiles == 0 || (batch && L.n_seg == 0);
+    const uint64_t n_sub = (L.len + SUB - 1) / SUB;
+    const uint64_t n_chunks = (n_sub + NCONS - 1) / NCONS;
+    const WsLayout W = layout_of(L.len, batch);
+    if (L.ws_bytes < W.total) return 2;
+    uint8_t *ws = reinterpret_cast<uint8_t *>(L.ws);
+    uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
+    const bool nothing = (A.n_patterns == 0) || n_sub == 0 || (batch && L.n_seg == 0);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 4;
-    DevProps pr = props_of(dev);
-    if (!pr.sms) return 4;
+    const DevProps pr = props_of(dev);
+    if (!pr.sms || !pr.coop) return 4;
 
-    // header: cleared first (the segment check below sets flags in it)
+    // header: cleared first when the segment check below sets flags in it
     if (batch && cudaMemsetAsync(hdr, 0, kHeaderBytes, L.stream) != cudaSuccess) return 4;
     {
-        uint64_t work = std::max<uint64_t>(n_tiles + 1, batch ? L.n_seg : 0);
+        const uint64_t work = std::max<uint64_t>(n_sub + 1, batch ? L.n_seg : 0);
         uint32_t blocks = (uint32_t)std::min<uint64_t>((work + 255) / 256, (uint64_t)pr.sms * 8);
         if (blocks == 0) blocks = 1;
-        init_kernel<<<blocks, 256, 0, L.stream>>>(hdr, tstat, tile_seg, nothing ? 0 : n_tiles,
+        init_kernel<<<blocks, 256, 0, L.stream>>>(hdr, reinterpret_cast<uint32_t *>(ws + W.tile_seg), nothing ? 0 : n_sub,
                                                    batch ? L.seg : nullptr, batch ? L.n_seg : 0, L.len,
-                                                   reinterpret_cast<unsigned long long *>(L.d_count), batch ? 0 : 1);
+                                                   reinterpret_cast<unsigned long long *>(L.d_count), batch ? 0 : 1,
+                                                   nothing ? 1 : 0);
         if (cudaGetLastError() != cudaSuccess) return 4;
     }
     if (nothing) return 0;
@@ -688,53 +924,60 @@ int launch_scan(const ScanLaunch &L) {
     kp.cap = L.capacity;
     kp.d_count = reinterpret_cast<unsigned long long *>(L.d_count);
     kp.hdr = hdr;
-    kp.tstat = tstat;
-    kp.tile_seg = tile_seg;
-    kp.n_tiles = n_tiles;
+    kp.desc = reinterpret_cast<SubDesc *>(ws + W.desc);
+    kp.sums = reinterpret_cast<unsigned long long *>(ws + W.sums);
+    kp.tile_seg = reinterpret_cast<const uint32_t *>(ws + W.tile_seg);
+    kp.records = reinterpret_cast<uint32_t *>(ws + W.records);
+    kp.n_sub = n_sub;
+    kp.n_chunks = n_chunks;
     uint32_t halo = A.max_len > 1 ? A.max_len - 1 : 0;
     halo = std::max<uint32_t>(16, align_up(std::min(halo, HALO_CAP), 16));
     kp.halo = halo;
-    kp.tbuf = align_up(TILE + halo, 128);
+    kp.slot_bytes = align_up(CHUNK + halo + 64, 128);
     kp.aligned = (reinterpret_cast<uintptr_t>(L.text) & 15) == 0;
-    kp.spin_budget = 4000000000ll;  // ~2 s of SM clock
+    kp.spin_budget = 4000000000ll;  // about 2 s of SM clock
 
-    // shared memory: tables first, then the groups
-    const uint32_t budget = (uint32_t)pr.smem_optin - 1024;
-    uint32_t group_bytes = align_up(2 * kp.tbuf + TILE * 4 + GT * 8 + WARPS_G * 8 + (SEGCAP + 1) * 8 +
-                                    (uint32_t)sizeof(GroupMisc), 128);
-    uint32_t ngroups = 4;
+    // shared memory: class map, bitmap, gram table, block state, ring, hot rows
+    const uint32_t budget = (uint32_t)pr.smem_optin;
     uint32_t off = 384;
     kp.off_bitmap = off;
     if (A.gram_len) off += (1u << A.bm_log2) / 8;
     off = align_up(off, 128);
     kp.off_grams = off;
-    uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * 16u : 0u;
-    const uint32_t groups_total = ngroups * group_bytes;
-    kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + groups_total <= budget) ? 1u : 0u;
+    const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * 16u : 0u;
+    const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + NSTAGE * kp.slot_bytes;
+    kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
     if (kp.grams_in_smem) off += gram_bytes;
     off = align_up(off, 128);
+    kp.off_misc = off;
+    off += align_up((uint32_t)sizeof(CtaMisc), 128);
+    kp.off_ring = off;
+    off += NSTAGE * kp.slot_bytes;
     kp.off_rows = off;
-    const uint32_t row_bytes = A.n_classes * 4;
-    uint32_t avail = budget > off + groups_total ? budget - off - groups_total : 0;
+    const uint32_t row_bytes = A.n_classes * (A.row16 ? 2u : 4u);
+    uint32_t avail = budget > off + 32 ? budget - off - 32 : 0;
     if (L.smem_budget) avail = std::min(avail, L.smem_budget);
-    uint32_t hot_avail = A.n_dense > A.hot_lo ? A.n_dense - A.hot_lo : 0;
+    const uint32_t hot_avail = A.n_dense > A.hot_lo ? A.n_dense - A.hot_lo : 0;
     kp.hot_n = std::min<uint32_t>(hot_avail, row_bytes ? avail / row_bytes : 0);
-    off += kp.hot_n * row_bytes;
-    off = align_up(off, 128);
-    kp.off_groups = off;
-    kp.group_bytes = group_bytes;
-    kp.ngroups = ngroups;
-    const uint32_t smem = off + groups_total;
-    if (smem > (uint32_t)pr.smem_optin) return 7;
-    uint64_t want = (n_tiles + ngroups - 1) / ngroups;
-    uint32_t grid = (uint32_t)std::min<uint64_t>(want, (uint64_t)pr.sms);
+    off += align_up(kp.hot_n * row_bytes + 16, 16);
+    const uint32_t smem = off;
+    if (smem > budget) return 7;
+    if (PB * 8 > NSTAGE * kp.slot_bytes) return 7;
+    uint32_t grid = (uint32_t)std::min<uint64_t>(n_chunks, (uint64_t)std::min(pr.sms, (int)kMaxGrid));
     if (grid == 0) grid = 1;
+    kp.rec_cap_cta = (uint32_t)std::min<uint64_t>(W.rec_slots / grid, 0xFFFFFFF0ull / grid);
+    kp.rec_slots = W.rec_slots;
 
-    if (A.gram_len == 0)
-        return batch ? launch_t<0, true>(kp, smem, grid, L.stream) : launch_t<0, false>(kp, smem, grid, L.stream);
-    if (A.gram_len == 4)
-        return batch ? launch_t<4, true>(kp, smem, grid, L.stream) : launch_t<4, false>(kp, smem, grid, L.stream);
-    return batch ? launch_t<8, true>(kp, smem, grid, L.stream) : launch_t<8, false>(kp, smem, grid, L.stream);
+    const bool r16 = A.row16 != 0;
+#define GLOP_LAUNCH(F)                                                                                   \
+    return batch ? (r16 ? launch_t<F, true, true>(kp, smem, grid, L.stream)                              \
+                        : launch_t<F, true, false>(kp, smem, grid, L.stream))                            \
+                 : (r16 ? launch_t<F, false, true>(kp, smem, grid, L.stream)                             \
+                        : launch_t<F, false, false>(kp, smem, grid, L.stream))
+    if (A.gram_len == 0) GLOP_LAUNCH(0);
+    if (A.gram_len == 4) GLOP_LAUNCH(4);
+    GLOP_LAUNCH(8);
+#undef GLOP_LAUNCH
 }
 
 }  // namespace glop

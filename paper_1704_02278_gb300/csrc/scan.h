@@ -1,4 +1,4 @@
-// scan.h -- launchers of the scan kernels (internal to libglop.so).
+// scan.h -- launcher of the scan kernel (internal to libglop.so).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -8,13 +8,16 @@
 namespace glop {
 
 // workspace header flags (uint32 at offset 0 of the workspace)
-enum : uint32_t { WS_TIMEOUT = 1u, WS_OVERFLOW = 2u, WS_EINVAL = 4u };
+// header word 11/12 hold the site and value of the first broken internal check
+enum : uint32_t { WS_TIMEOUT = 1u, WS_OVERFLOW = 2u, WS_EINVAL = 4u, WS_INTERNAL = 8u };
 
-// Geometry of one scan tile: 256 threads x 16 start offsets.
-constexpr uint32_t kGroupThreads = 256;
-constexpr uint32_t kOffsetsPerThread = 16;
-constexpr uint32_t kTile = kGroupThreads * kOffsetsPerThread;  // 4096 bytes
+// Geometry: a consumer warp scans 1 KiB sub-tiles (32 lanes x 32 start
+// offsets); 31 consumer warps share 31 KiB chunks brought in by one producer.
+constexpr uint32_t kSubTile = 1024;
+constexpr uint32_t kConsumers = 31;
+constexpr uint32_t kChunk = kSubTile * kConsumers;
 constexpr uint32_t kHeaderBytes = 256;
+constexpr uint32_t kMaxGrid = 1024;
 
 struct ScanLaunch {
     const GlopDevAutomaton *A;  // descriptor with device pointers (host copy)
@@ -31,6 +34,10 @@ struct ScanLaunch {
     uint32_t smem_budget;  // 0 = library default
 };
 
+// Workspace: header, one descriptor per sub-tile, block sums, (batch) the
+// first segment of every sub-tile, then scratch records of walked offsets
+// with a match -- room for one record per 8 text bytes.  A sub-tile whose
+// records do not fit is walked a second time instead; results stay exact.
 uint64_t workspace_bytes(uint64_t len, bool batch);
 // returns a glop_status value
 int launch_scan(const ScanLaunch &L);

@@ -36,7 +36,7 @@ def scan(text, seg, pat_buf, pat_offs, prefix_len=0):
     po = np.ascontiguousarray(pat_offs, dtype=np.uint64)
     out = ctypes.POINTER(ctypes.c_uint32)()
     cnt = ctypes.c_uint64()
-    stats = np.zeros(8, np.uint64)
+    stats = np.zeros(16, np.uint64)
     rc = lib.glop_hostcheck_scan(pb.ctypes.data, po.ctypes.data, len(po) - 1, prefix_len, t.ctypes.data,
                                  seg.ctypes.data, len(seg) - 1, ctypes.byref(out), ctypes.byref(cnt),
                                  stats.ctypes.data)
@@ -48,5 +48,6 @@ def scan(text, seg, pat_buf, pat_offs, prefix_len=0):
         lib.glop_hostcheck_free(out)
     else:
         arr = np.zeros((0, 3), np.uint32)
-    keys = ["n_states", "n_dense", "n_classes", "gram_len", "filter_pass", "gram_found"]
+    keys = ["n_states", "n_dense", "n_classes", "gram_len", "filter_pass", "gram_found", "dense_steps",
+            "chain_entries", "chain_bytes", "matched_offsets"]
     return arr, {k: int(stats[i]) for i, k in enumerate(keys)}

@@ -90,3 +90,14 @@ def test_files_slice():
     exp = oracle.batch(t, seg, p.csr())
     got, n = gpu_batch(p, t, seg)
     assert np.array_equal(got, exp)
+
+
+def test_dense_batch_overflow_scratch():
+    segs = [b"a" * 5000, b"ab" * 3000, b"a" * 70000, b"", b"ba" * 10]
+    seg = np.zeros(len(segs) + 1, np.uint64)
+    seg[1:] = np.cumsum([len(x) for x in segs])
+    text = b"".join(segs)
+    pats = [b"aaaa", b"abab", b"baba", b"aaaaa"]
+    exp = oracle.batch(text, seg, pats, method="naive")
+    got, _ = gpu_batch(pats, np.frombuffer(text, np.uint8), seg)
+    assert np.array_equal(got, exp)

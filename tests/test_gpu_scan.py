@@ -183,3 +183,14 @@ def test_scan_host_matches_device_scan():
     assert total == len(exp)
     assert np.array_equal(got, exp)
     a.close()
+
+
+def test_dense_matches_overflow_scratch():
+    """Every offset matches: the scratch records overflow and sub-tiles are walked again."""
+    text = np.full(1 << 20, ord("a"), np.uint8)
+    text[::1000] = ord("b")
+    pats = [b"aaaa", b"aaaaaaaa", b"baaa", b"aaaa"]
+    got, n = gpu_scan(pats, text)
+    exp = oracle.ac_mt(text, pats)
+    assert n == len(exp)
+    assert np.array_equal(got, exp)
