@@ -27,13 +27,16 @@ uint32_t rd32(const uint8_t *p, uint64_t avail) {
 
 struct WalkStats {
     uint64_t dense_steps = 0, chain_entries = 0, chain_bytes = 0, hot_steps = 0;
+    uint32_t iters = 0;  // loop iterations of the last walk
 };
 
 // deepest terminal state reached from state s with the next text byte at pos
 uint32_t walk(const HostAutomaton &A, const uint8_t *text, uint32_t s, uint64_t pos, uint64_t end, uint32_t t,
               WalkStats &ws) {
     const uint32_t C = A.n_classes;
+    ws.iters = 0;
     while (true) {
+        ++ws.iters;
         if (s < A.n_dense) {
             if (pos >= end) return t;
             ++ws.dense_steps;
@@ -81,9 +84,22 @@ extern "C" {
 // stats[5] = offsets found in the gram table; stats[6..8] = dense-row steps,
 // chain entries and chain bytes compared by all walks; stats[9] = offsets
 // with at least one match.  Returns a glop_status value.
+int glop_hostcheck_scan_iters(const uint8_t *pat, const uint64_t *poff, uint32_t npat, uint32_t prefix_len,
+                              const uint8_t *text, const uint64_t *seg, uint32_t nseg, uint32_t **out,
+                              uint64_t *count, uint64_t *stats, uint8_t *iters);
+
 int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat, uint32_t prefix_len,
                         const uint8_t *text, const uint64_t *seg, uint32_t nseg, uint32_t **out, uint64_t *count,
                         uint64_t *stats) {
+    return glop_hostcheck_scan_iters(pat, poff, npat, prefix_len, text, seg, nseg, out, count, stats, nullptr);
+}
+
+// As glop_hostcheck_scan; iters (one byte per text byte, may be NULL) receives
+// 255 for offsets that fail the start filter, else the walk's loop iterations
+// (0 when the gram table has no entry).
+int glop_hostcheck_scan_iters(const uint8_t *pat, const uint64_t *poff, uint32_t npat, uint32_t prefix_len,
+                              const uint8_t *text, const uint64_t *seg, uint32_t nseg, uint32_t **out,
+                              uint64_t *count, uint64_t *stats, uint8_t *iters) {
     *out = nullptr;
     *count = 0;
     HostAutomaton A;
@@ -105,7 +121,9 @@ int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat,
                 uint32_t w1 = rd32(text + i + 4, hi - i - 4) & glop_w1_mask(g);
                 uint32_t h = glop_gram_hash(w0, w1);
                 uint32_t bi = glop_bitmap_index(h, A.bm_log2);
+                if (iters) iters[i] = 255;
                 if (!((A.bitmap[bi >> 5] >> (bi & 31)) & 1u)) continue;
+                if (iters) iters[i] = 0;
                 ++passed;
                 uint32_t m = (1u << A.ht_log2) - 1, slot = glop_table_slot(h, A.ht_log2), v = 0;
                 while (A.grams[slot].val) {
@@ -122,6 +140,7 @@ int glop_hostcheck_scan(const uint8_t *pat, const uint64_t *poff, uint32_t npat,
                 pos = i;
             }
             t = walk(A, text, s, pos, hi, t, wst);
+            if (iters) iters[i] = (uint8_t)std::min<uint32_t>(wst.iters, 254);
             if (t) ++matched;
             for (uint32_t k = A.cum_off[t]; t && k < A.cum_off[t + 1]; ++k) {
                 res.push_back(sg);

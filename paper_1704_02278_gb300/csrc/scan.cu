@@ -56,6 +56,8 @@ constexpr uint32_t PB = 4096;  // sub-tiles per phase-B piece
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr unsigned long long END_TICKET = ~0ull;
 constexpr uint32_t REC_OVERFLOW = 0xFFFFFFFFu;
+constexpr uint32_t QCAP = 128;   // survivors per walk batch of one warp
+constexpr uint32_t QBYTES = QCAP * 10;  // per-warp queue: offsets (u16), states (u32), walk bounds (u32)
 
 struct SubDesc {
     uint32_t rec_start, n_rec;  // absolute record index; n_rec == REC_OVERFLOW: records not stored
@@ -91,7 +93,7 @@ struct KParams {
     uint64_t rec_slots;    // record slots in the workspace
     uint64_t n_sub, n_chunks;
     uint32_t halo, slot_bytes, hot_n, grams_in_smem, aligned;
-    uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring;
+    uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring, off_q;
     long long spin_budget;
 };
 
@@ -256,58 +258,61 @@ __device__ __forceinline__ uint32_t row_entry(const GlopDevAutomaton &A, const v
                        : (uint32_t)__ldg(reinterpret_cast<const int32_t *>(A.rows) + (size_t)s * C + cl);
 }
 
-// Deepest terminal state reached from state s with the next text byte at
-// sub-tile position pos; the walk never reads at or past end.
+// One step of a walk from state s with the next text byte at sub-tile
+// position pos, never reading at or past end: a dense-row transition or one
+// chain piece.  t is the deepest terminal state passed so far.  Returns true
+// when the walk is over (t is then final).
 template <bool ROW16>
-__device__ uint32_t walk(const GlopDevAutomaton &A, const uint8_t *cls_s, const void *rows_s, uint32_t hot_n,
-                         const TextView &v, uint32_t s, uint32_t pos, uint32_t end, uint32_t t, uint32_t *hdr) {
-    const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf);
-    while (true) {
-        if (s >= A.n_states) { fail_check(hdr, 1, s); return 0u; }
-        if (s < A.n_dense) {
-            if (pos >= end) return t;
-            const uint32_t e = row_entry<ROW16>(A, rows_s, hot_n, s, cls_s[tbyte(v, pos)], hdr);
-            if (!e) return t;
-            s = e & GLOP_STATE_MASK;
-            ++pos;
-            if (e & GLOP_TERM) t = s;
-        } else {
-            const uint4 *rec = reinterpret_cast<const uint4 *>(A.chain) + 2 * (size_t)(s - A.n_dense);
-            const uint4 c0 = __ldg(rec), c1 = __ldg(rec + 1);
-            const uint32_t exitv = c1.x, term = c1.y, tm = c1.z & 0xFFFFu, rem = (c1.z >> 16) & 0xFFu,
-                           nst = c1.z >> 24;
-            const uint32_t lim = min(rem, end - pos);
-            uint32_t m;
-            if (pos + 20 <= v.n_stage) {
-                const uint32_t x0 = tword(b32, pos) ^ c0.x, x1 = tword(b32, pos + 4) ^ c0.y,
-                               x2 = tword(b32, pos + 8) ^ c0.z, x3 = tword(b32, pos + 12) ^ c0.w;
-                m = x0   ? (uint32_t)(__ffs(x0) - 1) >> 3
-                    : x1 ? 4 + ((uint32_t)(__ffs(x1) - 1) >> 3)
-                    : x2 ? 8 + ((uint32_t)(__ffs(x2) - 1) >> 3)
-                    : x3 ? 12 + ((uint32_t)(__ffs(x3) - 1) >> 3)
-                         : 16u;
-                m = min(m, lim);
-            } else {
-                m = 0;
-                while (m < lim) {
-                    const uint32_t w = m < 4 ? c0.x : m < 8 ? c0.y : m < 12 ? c0.z : c0.w;
-                    if (tbyte(v, pos + m) != ((w >> (8 * (m & 3))) & 0xFFu)) break;
-                    ++m;
-                }
-            }
-            const uint32_t r = min(m, nst);
-            const uint32_t hit = tm & ((2u << r) - 1u);
-            if (hit) t = s + 31 - __clz(hit);
-            else if (term) t = term;
-            if (exitv && m == rem) {
-                s = exitv & GLOP_STATE_MASK;
-                pos += m;
-                if (exitv & GLOP_TERM) t = s;
-                continue;
-            }
-            return t;
+__device__ __forceinline__ bool step(const GlopDevAutomaton &A, const uint8_t *cls_s, const void *rows_s,
+                                     uint32_t hot_n, const TextView &v, uint32_t &s, uint32_t &pos, uint32_t end,
+                                     uint32_t &t, uint32_t *hdr) {
+    if (s >= A.n_states) {
+        fail_check(hdr, 1, s);
+        t = 0;
+        return true;
+    }
+    if (s < A.n_dense) {
+        if (pos >= end) return true;
+        const uint32_t e = row_entry<ROW16>(A, rows_s, hot_n, s, cls_s[tbyte(v, pos)], hdr);
+        if (!e) return true;
+        s = e & GLOP_STATE_MASK;
+        ++pos;
+        if (e & GLOP_TERM) t = s;
+        return false;
+    }
+    const uint4 *rec = reinterpret_cast<const uint4 *>(A.chain) + 2 * (size_t)(s - A.n_dense);
+    const uint4 c0 = __ldg(rec), c1 = __ldg(rec + 1);
+    const uint32_t exitv = c1.x, term = c1.y, tm = c1.z & 0xFFFFu, rem = (c1.z >> 16) & 0xFFu, nst = c1.z >> 24;
+    const uint32_t lim = min(rem, end - pos);
+    uint32_t m;
+    if (pos + 20 <= v.n_stage) {
+        const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf);
+        const uint32_t x0 = tword(b32, pos) ^ c0.x, x1 = tword(b32, pos + 4) ^ c0.y, x2 = tword(b32, pos + 8) ^ c0.z,
+                       x3 = tword(b32, pos + 12) ^ c0.w;
+        m = 16u;
+        if (x3) m = 12 + ((uint32_t)(__ffs(x3) - 1) >> 3);
+        if (x2) m = 8 + ((uint32_t)(__ffs(x2) - 1) >> 3);
+        if (x1) m = 4 + ((uint32_t)(__ffs(x1) - 1) >> 3);
+        if (x0) m = (uint32_t)(__ffs(x0) - 1) >> 3;
+        m = min(m, lim);
+    } else {
+        m = 0;
+        while (m < lim) {
+            const uint32_t w = m < 4 ? c0.x : m < 8 ? c0.y : m < 12 ? c0.z : c0.w;
+            if (tbyte(v, pos + m) != ((w >> (8 * (m & 3))) & 0xFFu)) break;
+            ++m;
         }
     }
+    const uint32_t hit = tm & ((2u << min(m, nst)) - 1u);
+    if (hit) t = s + 31 - __clz(hit);
+    else if (term) t = term;
+    if (exitv && m == rem) {
+        s = exitv & GLOP_STATE_MASK;
+        pos += m;
+        if (exitv & GLOP_TERM) t = s;
+        return false;
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -403,10 +408,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     const uint32_t w1mask = FILT == 8 ? glop_w1_mask(g) : 0u;
     const uint32_t bsh = 32u - A.bm_log2;
     const uint32_t htmask = (1u << A.ht_log2) - 1u;
-    constexpr uint32_t REC_W = BATCH ? 3u : 2u;  // record size in uint32
+    constexpr uint32_t REC_W = BATCH ? 4u : 3u;  // record size in uint32
 
-    // walk from sub-tile offset off (the text ends for this walk at endr)
-    auto walk_at = [&](const TextView &v, uint32_t off, uint32_t endr) -> uint32_t {
+    // Start of the walk from sub-tile offset off (walk bound endr): the state
+    // reached by the first gram_len bytes, | GLOP_TERM when it is terminal;
+    // without a start filter the initial state, encoded GLOP_TERM (state 0 is
+    // never terminal).  0 when no pattern can start here.
+    auto probe = [&](const TextView &v, uint32_t off, uint32_t endr) -> uint32_t {
         if (FILT) {
             if (off + g > endr) return 0u;
             uint32_t w0 = 0, w1 = 0;
@@ -423,18 +431,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             }
             uint32_t h = w0 * GLOP_HASH_M0;
             if (FILT == 8) h ^= w1 * GLOP_HASH_M1;
-            uint32_t slot = glop_table_slot(h, A.ht_log2), val = 0;
+            uint32_t slot = glop_table_slot(h, A.ht_log2);
             while (true) {
                 const uint4 e = *reinterpret_cast<const uint4 *>(grams + slot);
-                if (!e.z) break;
-                if (e.x == w0 && e.y == w1) { val = e.z; break; }
+                if (!e.z) return 0u;
+                if (e.x == w0 && e.y == w1) return e.z;
                 slot = (slot + 1) & htmask;
             }
-            if (!val) return 0u;
-            const uint32_t s = val & GLOP_STATE_MASK;
-            return walk<ROW16>(A, cls_s, rows_s, p.hot_n, v, s, off + g, endr, (val & GLOP_TERM) ? s : 0u, p.hdr);
         }
-        return walk<ROW16>(A, cls_s, rows_s, p.hot_n, v, 0u, off, endr, 0u, p.hdr);
+        return off < endr ? GLOP_TERM : 0u;
     };
 
     // start filter: bit j of the result = offset 32*lane + j of the sub-tile may start a match
@@ -532,16 +537,11 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         return L <= SEGW;
     };
 
-    // Expand up to 32 matching offsets held one per lane (state t, fields f0/f1)
-    // into output slots o, o+1, ...: all patterns of an offset, offsets in lane
-    // order.  Returns the number of outputs.
-    auto expand = [&](uint32_t t, uint32_t f0, uint32_t f1, unsigned long long o) -> uint32_t {
-        uint32_t lo = 0, c = 0;
-        if (t >= A.n_states) { if (t) fail_check(p.hdr, 2, t); t = 0; }
-        if (t) {
-            lo = __ldg(A.cum_off + t);
-            c = __ldg(A.cum_off + t + 1) - lo;
-        }
+    // Expand up to 32 matching offsets held one per lane (output list lo..lo+c
+    // of the deepest terminal state, fields f0/f1) into output slots o, o+1,
+    // ...: all patterns of an offset, offsets in lane order.  Returns the
+    // number of outputs.
+    auto expand = [&](uint32_t lo, uint32_t c, uint32_t f0, uint32_t f1, unsigned long long o) -> uint32_t {
         const uint32_t incl = warp_incl_scan(c, lane), excl = incl - c, tot = __shfl_sync(FULL, incl, 31);
         for (uint32_t s0 = 0; s0 < tot; s0 += 32) {
             const uint32_t slot = s0 + lane;
@@ -565,18 +565,28 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         return tot;
     };
 
-    // Walk every survivor of sub-tile j.  Record mode: (offset, state) records
-    // into this block's scratch slice and a descriptor.  Direct mode (output
-    // position known): expand straight into the output.
-    auto process = [&](uint64_t j, const TextView &v, uint32_t cw, bool direct, unsigned long long obase) {
+    // Walk every survivor of sub-tile j, in batches of up to QCAP survivors:
+    // (1) survivor offsets into the warp's queue, (2) probe pass: gram table,
+    // keeping the survivors a pattern can start at, in offset order, (3) walk
+    // pass: each lane takes the next queued walk as soon as its previous one
+    // ends, (4) in offset order, record mode writes (offset, output list)
+    // records to this block's scratch slice and the sub-tile descriptor;
+    // direct mode (output position known) expands straight into the output.
+    auto process = [&](uint64_t j, const TextView &v, uint32_t qw, bool direct, unsigned long long obase) {
         const uint64_t s0 = j * SUB;
         const uint64_t avail = p.len - s0;
         const uint32_t sub_len = (uint32_t)min((uint64_t)SUB, avail);
+        const uint32_t endsub = (uint32_t)min(avail, (uint64_t)0xFFFFFFFFu);
         bool onchip = true;
-        if (BATCH) onchip = load_segs(cw, j);
+        if (BATCH) onchip = load_segs(qw, j);
         const uint32_t mask = filter(v, sub_len, avail);
         const uint32_t n = __popc(mask);
         const uint32_t incl = warp_incl_scan(n, lane), excl = incl - n, total = __shfl_sync(FULL, incl, 31);
+        uint8_t *qbase = smem + p.off_q + qw * QBYTES;
+        uint16_t *qoff = reinterpret_cast<uint16_t *>(qbase);
+        uint32_t *qst = reinterpret_cast<uint32_t *>(qbase + QCAP * 2);
+        uint32_t *qend = reinterpret_cast<uint32_t *>(qbase + QCAP * 6);
+        const uint32_t lt = (1u << lane) - 1u;
         uint32_t rbase = 0;
         bool ovf = false;
         if (!direct) {
@@ -588,43 +598,116 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         uint32_t *recs = p.records + (size_t)rabs * REC_W;
         uint32_t nrec = 0;
         unsigned long long nmatch = 0, o = obase;
-        for (uint32_t r0 = 0; r0 < total; r0 += 32) {
-            const uint32_t i = r0 + lane;
-            const uint32_t ow = owner_of(excl, i);
-            const uint32_t m_o = __shfl_sync(FULL, mask, ow), e_o = __shfl_sync(FULL, excl, ow);
-            uint32_t t = 0, f0 = 0, f1 = 0;
-            if (i < total) {
-                uint32_t off = ow * 32 + __fns(m_o, 0, (int)(i - e_o + 1));
-                if (off >= SUB) { fail_check(p.hdr, 3, off); off = 0; }
-                const uint64_t iabs = s0 + off;
-                uint32_t si = 0;
-                uint64_t sstart = 0, send = p.len;
-                bool in = true;
-                if (BATCH) in = seg_of(cw, onchip, iabs, si, sstart, send);
-                if (in) t = walk_at(v, off, (uint32_t)min(send - s0, (uint64_t)0xFFFFFFFFu));
-                if (BATCH) {
-                    f0 = si;
-                    f1 = (uint32_t)(iabs - sstart);
-                } else {
-                    f0 = (uint32_t)iabs;
+        for (uint32_t b0 = 0; b0 < total; b0 += QCAP) {
+            const uint32_t nb = min(QCAP, total - b0);
+            // (1) survivor offsets
+            if (excl < b0 + nb && excl + n > b0) {
+                uint32_t m = mask, idx = excl;
+                while (m) {
+                    const uint32_t bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    const uint32_t rel = idx - b0;
+                    if (rel < nb) qoff[rel] = (uint16_t)(32 * lane + bit);
+                    ++idx;
                 }
             }
-            if (direct) {
-                o += expand(t, f0, f1, o);
-            } else {
-                const uint32_t b = __ballot_sync(FULL, t != 0);
-                if (t) {
-                    const uint32_t pos = nrec + __popc(b & ((1u << lane) - 1u));
-                    GLOP_CK(p.hdr, t < A.n_states, 26, t) nmatch += __ldg(A.cum_off + t + 1) - __ldg(A.cum_off + t);
-                    GLOP_CK(p.hdr, ovf || (uint64_t)rabs + pos < p.rec_slots, 27, rabs + pos)
-                    if (!ovf) {
-                        uint32_t *rp = recs + (size_t)pos * REC_W;
-                        rp[0] = f0;
-                        if (BATCH) { rp[1] = f1; rp[2] = t; } else { rp[1] = t; }
+            __syncwarp();
+            // (2) probe pass (in place: entry i moves to position <= i)
+            uint32_t nw = 0;
+            for (uint32_t r0 = 0; r0 < nb; r0 += 32) {
+                const uint32_t i = r0 + lane;
+                uint32_t off = 0, val = 0, endr = endsub;
+                if (i < nb) {
+                    off = qoff[i];
+                    bool in = true;
+                    if (BATCH) {
+                        uint32_t si;
+                        uint64_t sstart, send;
+                        in = seg_of(qw, onchip, s0 + off, si, sstart, send);
+                        endr = in ? (uint32_t)min(send - s0, (uint64_t)0xFFFFFFFFu) : 0u;
+                    }
+                    if (in) val = probe(v, off, endr);
+                }
+                const uint32_t bm = __ballot_sync(FULL, val != 0);
+                __syncwarp();
+                if (val) {
+                    const uint32_t q = nw + __popc(bm & lt);
+                    qoff[q] = (uint16_t)off;
+                    qst[q] = val;
+                    if (BATCH) qend[q] = endr;
+                }
+                nw += __popc(bm);
+            }
+            __syncwarp();
+            // (3) walk pass: lanes refill from the queue as their walks end
+            {
+                uint32_t nxt = 0, qi = 0, st = 0, pos = 0, t = 0, endw = endsub;
+                bool have = false;
+                while (true) {
+                    const uint32_t wm = __ballot_sync(FULL, !have);
+                    if (!have) {
+                        qi = nxt + __popc(wm & lt);
+                        if (qi < nw) {
+                            const uint32_t val = qst[qi];
+                            st = val & GLOP_STATE_MASK;
+                            t = (val & GLOP_TERM) ? st : 0u;
+                            pos = qoff[qi] + g;
+                            if (BATCH) endw = qend[qi];
+                            have = true;
+                        }
+                    }
+                    nxt += __popc(wm);
+                    if (!__any_sync(FULL, have)) break;
+                    if (have && step<ROW16>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr)) {
+                        qst[qi] = t;
+                        have = false;
                     }
                 }
-                nrec += __popc(b);
             }
+            __syncwarp();
+            // (4) records or direct output, in offset order
+            for (uint32_t r0 = 0; r0 < nw; r0 += 32) {
+                const uint32_t i = r0 + lane;
+                uint32_t t = 0, f0 = 0, f1 = 0, lo = 0, c = 0;
+                if (i < nw) {
+                    t = qst[i];
+                    if (t >= A.n_states) {
+                        fail_check(p.hdr, 2, t);
+                        t = 0;
+                    }
+                    if (t) {
+                        lo = __ldg(A.cum_off + t);
+                        c = __ldg(A.cum_off + t + 1) - lo;
+                        const uint64_t iabs = s0 + qoff[i];
+                        if (BATCH) {
+                            uint32_t si = 0;
+                            uint64_t sstart = 0, send = 0;
+                            seg_of(qw, onchip, iabs, si, sstart, send);
+                            f0 = si;
+                            f1 = (uint32_t)(iabs - sstart);
+                        } else {
+                            f0 = (uint32_t)iabs;
+                        }
+                    }
+                }
+                if (direct) {
+                    o += expand(lo, c, f0, f1, o);
+                } else {
+                    const uint32_t b = __ballot_sync(FULL, t != 0);
+                    if (t) {
+                        const uint32_t q = nrec + __popc(b & lt);
+                        nmatch += c;
+                        GLOP_CK(p.hdr, ovf || (uint64_t)rabs + q < p.rec_slots, 27, rabs + q)
+                        if (!ovf) {
+                            uint32_t *rp = recs + (size_t)q * REC_W;
+                            if (BATCH) *reinterpret_cast<uint4 *>(rp) = make_uint4(f0, f1, lo, c);
+                            else { rp[0] = f0; rp[1] = lo; rp[2] = c; }
+                        }
+                    }
+                    nrec += __popc(b);
+                }
+            }
+            __syncwarp();
         }
         if (!direct) {
             nmatch = warp_sum64(nmatch);
@@ -796,13 +879,17 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 const uint32_t *recs = p.records + (size_t)dr.x * REC_W;
                 for (uint32_t r0 = 0; r0 < dr.y; r0 += 32) {
                     const uint32_t r = r0 + lane;
-                    uint32_t t = 0, f0 = 0, f1 = 0;
+                    uint32_t f0 = 0, f1 = 0, lo = 0, c = 0;
                     if (r < dr.y) {
                         const uint32_t *rp = recs + (size_t)r * REC_W;
-                        f0 = __ldcg(rp);
-                        if (BATCH) { f1 = __ldcg(rp + 1); t = __ldcg(rp + 2); } else { t = __ldcg(rp + 1); }
+                        if (BATCH) {
+                            const uint4 x = __ldcg(reinterpret_cast<const uint4 *>(rp));
+                            f0 = x.x; f1 = x.y; lo = x.z; c = x.w;
+                        } else {
+                            f0 = __ldcg(rp); lo = __ldcg(rp + 1); c = __ldcg(rp + 2);
+                        }
                     }
-                    o += expand(t, f0, f1, o);
+                    o += expand(lo, c, f0, f1, o);
                 }
             } else {
                 // the records did not fit: walk the sub-tile again from global memory
@@ -876,7 +963,7 @@ WsLayout layout_of(uint64_t len, bool batch) {
     uint64_t after = w.tile_seg + (batch ? 4 * (n_sub + 1) : 0);
     w.records = (after + 255) / 256 * 256;
     w.rec_slots = std::max<uint64_t>(len / 8, 4096);
-    const uint64_t rec_bytes = batch ? 12 : 8;
+    const uint64_t rec_bytes = batch ? 16 : 12;
     w.total = (w.records + w.rec_slots * rec_bytes + 255) / 256 * 256;
     return w;
 }
@@ -945,7 +1032,7 @@ int launch_scan(const ScanLaunch &L) {
     off = align_up(off, 128);
     kp.off_grams = off;
     const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * 16u : 0u;
-    const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + NSTAGE * kp.slot_bytes;
+    const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + NSTAGE * kp.slot_bytes + 32 * QBYTES;
     kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
     if (kp.grams_in_smem) off += gram_bytes;
     off = align_up(off, 128);
@@ -953,6 +1040,9 @@ int launch_scan(const ScanLaunch &L) {
     off += align_up((uint32_t)sizeof(CtaMisc), 128);
     kp.off_ring = off;
     off += NSTAGE * kp.slot_bytes;
+    kp.off_q = off;
+    off += 32 * QBYTES;
+    off = align_up(off, 128);
     kp.off_rows = off;
     const uint32_t row_bytes = A.n_classes * (A.row16 ? 2u : 4u);
     uint32_t avail = budget > off + 32 ? budget - off - 32 : 0;
