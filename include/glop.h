@@ -184,6 +184,28 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
                            uint64_t capacity, uint64_t *h_count, void *d_staging, uint64_t staging_bytes,
                            glop_stream_t stream);
 
+/*
+ * glop_scan_noalloc -- glop_scan for callers that cannot allocate device
+ * memory at scan time (their device memory belongs to another allocator, or
+ * their loop must not pay for an allocation's implicit synchronisation).  The
+ * paper has no counterpart for this entry point.
+ *
+ * Arguments and results are those of glop_scan, without the workspace: the
+ * scratch memory is a 25 MiB device array that the library reserves on every
+ * device that loads it (held until the process exits).  len must be at most
+ * 16 MiB (16777216); longer texts return GLOP_EINVAL before anything is
+ * queued.  The call allocates nothing.
+ *
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.  Every
+ * call uses the same array and leaves its contents behind: two calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race on it and give wrong results.  Serialise them, e.g. on one stream.
+ * Per-call state in the array is reset by the call itself.
+ */
+glop_status glop_scan_noalloc(glop_handle h, const uint8_t *d_text, uint64_t len, glop_match *d_matches,
+                              uint64_t capacity, uint64_t *d_count, glop_stream_t stream);
+
 /* glop_destroy -- free the automaton's device memory.  No scan using h may
  * still be in flight.  NULL is accepted. */
 glop_status glop_destroy(glop_handle h);

@@ -35,7 +35,7 @@ OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 # Exported symbols of include/glop.h
 SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_workspace_size", "glop_scan",
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
-           "glop_scan_host", "glop_destroy", "glop_status_str"]
+           "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc"]
 
 
 class GlopError(RuntimeError):
@@ -90,6 +90,8 @@ def lib():
         L.glop_scan_host_staging_size.argtypes = [vp, u64, u64, ctypes.POINTER(u64)]
         L.glop_scan_host.restype = ctypes.c_int
         L.glop_scan_host.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(u64), vp, u64, vp]
+        L.glop_scan_noalloc.restype = ctypes.c_int
+        L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
         L.glop_destroy.restype = ctypes.c_int
         L.glop_destroy.argtypes = [vp]
         L.glop_status_str.restype = ctypes.c_char_p
