@@ -180,6 +180,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-segment-steps", type=int, default=1)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -218,15 +219,20 @@ def main():
     else:
         m0, M = a.scan_batch(text, seg, stream=stream)
     rec = 2 if seg is None else 3
-    matches = torch.empty((max(M, 1), rec), dtype=torch.int32, device=dev)
     del m0
+    torch.cuda.empty_cache()
+    matches = torch.empty((max(M, 1), rec), dtype=torch.int32, device=dev)
     ws_buf = a.workspace(N, dev, None if seg is None else w.seg.size - 1)
+    plan = None
+    if seg is not None:
+        # a batch step is one replay of the captured scan: a single graph launch over every segment
+        plan = glop.Plan(a, text, matches, count, seg_offsets=seg, stream=stream)
 
     def step():
-        if seg is None:
-            a.scan_into(text, matches, count, workspace=ws_buf, stream=stream)
+        if plan is not None:
+            plan.launch(stream)
         else:
-            a.scan_batch_into(text, seg, matches, count, workspace=ws_buf, stream=stream)
+            a.scan_into(text, matches, count, workspace=ws_buf, stream=stream)
 
     clocks = ClockSampler(local).start()
     with torch.cuda.stream(stream):
@@ -271,6 +277,50 @@ def main():
     avg_launch_ms = statistics.mean(per)
     achieved = algo_bytes / (avg_launch_ms / 1e3) / 1e9
 
+    # batches: the same work as plain per-segment glop_scan launches on the same stream
+    per_segment = None
+    if seg is not None and args.per_segment_steps > 0:
+        import ctypes
+        L = glop.lib()
+        segs = w.seg
+        nseg = len(segs) - 1
+        per_cnt = torch.zeros(nseg, dtype=torch.int64, device=dev)
+        big = int(np.max(np.diff(segs))) if nseg else 0
+        ws1 = torch.empty(a.workspace_bytes(big), dtype=torch.uint8, device=dev)
+        out1 = torch.empty((max(M, 1), 2), dtype=torch.int32, device=dev)
+        tp, op, cp, wp = text.data_ptr(), out1.data_ptr(), per_cnt.data_ptr(), ws1.data_ptr()
+        h, sh = a.handle, stream.cuda_stream
+        lens = np.diff(segs).astype(np.uint64)
+        starts = segs[:-1].astype(np.uint64)
+
+        def per_segment_pass(bases, caps):
+            for f in range(nseg):
+                rc = L.glop_scan(h, tp + int(starts[f]), int(lens[f]), op + 8 * int(bases[f]), int(caps[f]),
+                                 cp + 8 * f, wp, ws1.numel(), sh)
+                assert rc == 0, rc
+        # first pass: counts only; then every file writes at its place in one output, as the batch does
+        per_segment_pass(np.zeros(nseg, np.int64), np.zeros(nseg, np.int64))
+        stream.synchronize()
+        caps = per_cnt.cpu().numpy()
+        bases = np.concatenate([[0], np.cumsum(caps)[:-1]])
+        per_segment_pass(bases, caps)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.per_segment_steps):
+            per_segment_pass(bases, caps)
+        e1.record(stream)
+        stream.synchronize()
+        wall = (time.perf_counter() - t0) / args.per_segment_steps
+        gpu_ms = e0.elapsed_time(e1) / args.per_segment_steps
+        assert int(per_cnt.sum().item()) == M
+        per_segment = {"launches_per_step": 2 * nseg, "ms_per_step": round(max(gpu_ms, wall * 1e3), 3),
+                       "gpu_ms_per_step": round(gpu_ms, 3), "host_ms_per_step": round(wall * 1e3, 3),
+                       "value": round(8.0 * N / (max(gpu_ms, wall * 1e3) / 1e3) / 1e9, 3), "unit": "Gbit/s",
+                       "note": "plain glop_scan per segment from Python on one stream (counts only kept per file)"}
+        del out1, ws1
+
     # end to end through the C ABI with host buffers (pinned text in, matches out)
     e2e = None
     if seg is None and args.e2e_steps > 0:
@@ -313,10 +363,13 @@ def main():
                              % (rec * 4, which)},
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
+        "launch": "cuda graph (memset + init + scan kernel) per step" if plan is not None else "glop_scan per step",
         "hbm_input_frac": round(N / (avg_launch_ms / 1e3) / 1e9 / hbm, 4),
     }
     if e2e:
         line["e2e"] = e2e
+    if per_segment:
+        line["per_segment_launches"] = per_segment
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

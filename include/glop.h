@@ -185,6 +185,27 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
                            glop_stream_t stream);
 
 /*
+ * Plans: a whole scan (glop_scan, or glop_scan_batch when d_seg_offsets is
+ * not NULL) captured once into a CUDA graph for fixed buffers, then replayed
+ * with a single graph launch -- the batched form of the paper's streamed
+ * kernels (Sec. 6: the CPU streams the next batch while a kernel runs).
+ *
+ * glop_plan_create captures the scan's work on stream (nothing runs) and
+ * instantiates the graph; every argument is as for glop_scan /
+ * glop_scan_batch and must stay valid for the plan's lifetime.  Errors as
+ * for those calls; GLOP_ECUDA if capture or instantiation fails.
+ * glop_plan_launch queues one replay on stream (any stream of the device).
+ * glop_plan_destroy frees the graph (NULL accepted); no replay may be in
+ * flight.
+ */
+typedef struct glop_plan_s *glop_plan;
+glop_status glop_plan_create(glop_handle h, const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
+                             uint32_t n_segments, void *d_matches, uint64_t capacity, uint64_t *d_count,
+                             void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream, glop_plan *out);
+glop_status glop_plan_launch(glop_plan plan, glop_stream_t stream);
+glop_status glop_plan_destroy(glop_plan plan);
+
+/*
  * glop_scan_noalloc -- glop_scan for callers that cannot allocate device
  * memory at scan time (their device memory belongs to another allocator, or
  * their loop must not pay for an allocation's implicit synchronisation).  The

@@ -20,7 +20,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["Automaton", "GlopError", "lib", "library_path", "STATUS"]
+__all__ = ["Automaton", "Plan", "GlopError", "lib", "library_path", "STATUS"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # GLOP_LIBRARY selects another build of the library (e.g. the bounds-checked debug build)
@@ -35,7 +35,8 @@ OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 # Exported symbols of include/glop.h
 SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_workspace_size", "glop_scan",
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
-           "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc"]
+           "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc", "glop_plan_create",
+           "glop_plan_launch", "glop_plan_destroy"]
 
 
 class GlopError(RuntimeError):
@@ -90,6 +91,12 @@ def lib():
         L.glop_scan_host_staging_size.argtypes = [vp, u64, u64, ctypes.POINTER(u64)]
         L.glop_scan_host.restype = ctypes.c_int
         L.glop_scan_host.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(u64), vp, u64, vp]
+        L.glop_plan_create.restype = ctypes.c_int
+        L.glop_plan_create.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, u64, vp, ctypes.POINTER(vp)]
+        L.glop_plan_launch.restype = ctypes.c_int
+        L.glop_plan_launch.argtypes = [vp, vp]
+        L.glop_plan_destroy.restype = ctypes.c_int
+        L.glop_plan_destroy.argtypes = [vp]
         L.glop_scan_noalloc.restype = ctypes.c_int
         L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
         L.glop_destroy.restype = ctypes.c_int
@@ -279,6 +286,48 @@ class Automaton:
             lib().glop_destroy(self._h)
             self._h = None
         self._ws = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A scan captured into a CUDA graph for fixed device buffers; ``launch()`` replays it with one graph launch.
+
+    ``seg_offsets`` None: single-buffer scan, ``matches`` (cap, 2) int32; else a batch over segments, ``matches``
+    (cap, 3) int32.  All tensors must outlive the plan.  ``stream`` must be a non-default torch stream."""
+
+    def __init__(self, automaton: Automaton, text, matches, count, seg_offsets=None, stream=None):
+        torch = _torch()
+        self._keep = (automaton, text, matches, count, seg_offsets)
+        n = text.numel()
+        nseg = None if seg_offsets is None else seg_offsets.numel() - 1
+        self.workspace = torch.empty(automaton.workspace_bytes(n, nseg), dtype=torch.uint8, device=text.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=text.device)
+        h = ctypes.c_void_p()
+        _check(lib().glop_plan_create(automaton.handle, text.data_ptr() if n else None, n,
+                                      None if seg_offsets is None else seg_offsets.data_ptr(), nseg or 0,
+                                      matches.data_ptr(), matches.shape[0], count.data_ptr(),
+                                      self.workspace.data_ptr(), self.workspace.numel(), self.stream.cuda_stream,
+                                      ctypes.byref(h)), "glop_plan_create")
+        self._h = h
+
+    def launch(self, stream=None) -> None:
+        s = stream if stream is not None else self.stream
+        _check(lib().glop_plan_launch(self._h, s.cuda_stream), "glop_plan_launch")
+
+    def status(self, stream=None) -> int:
+        s = stream if stream is not None else self.stream
+        cnt = ctypes.c_uint64()
+        return int(lib().glop_scan_status(self.workspace.data_ptr(), s.cuda_stream, ctypes.byref(cnt)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().glop_plan_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -273,6 +273,58 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
     return GLOP_OK;
 }
 
+struct glop_plan_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+glop_status glop_plan_create(glop_handle h, const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
+                             uint32_t n_segments, void *d_matches, uint64_t capacity, uint64_t *d_count,
+                             void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream, glop_plan *out) {
+    if (!out || !stream) return GLOP_EINVAL;  // capture needs a real stream, not the legacy default stream
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    glop_plan p = new (std::nothrow) glop_plan_s();
+    if (!p) return GLOP_ENOMEM;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        delete p;
+        return GLOP_ECUDA;
+    }
+    glop_status s = d_seg_offsets
+                        ? glop_scan_batch(h, d_text, text_len, d_seg_offsets, n_segments,
+                                          reinterpret_cast<glop_batch_match *>(d_matches), capacity, d_count,
+                                          d_workspace, workspace_bytes, stream)
+                        : glop_scan(h, d_text, text_len, reinterpret_cast<glop_match *>(d_matches), capacity, d_count,
+                                    d_workspace, workspace_bytes, stream);
+    cudaError_t e = cudaStreamEndCapture(st, &p->graph);
+    if (s != GLOP_OK || e != cudaSuccess) {
+        if (p->graph) cudaGraphDestroy(p->graph);
+        delete p;
+        cudaGetLastError();
+        return s != GLOP_OK ? s : GLOP_ECUDA;
+    }
+    if (cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(p->graph);
+        delete p;
+        cudaGetLastError();
+        return GLOP_ECUDA;
+    }
+    *out = p;
+    return GLOP_OK;
+}
+
+glop_status glop_plan_launch(glop_plan plan, glop_stream_t stream) {
+    if (!plan) return GLOP_EINVAL;
+    return cuda_ok(cudaGraphLaunch(plan->exec, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+glop_status glop_plan_destroy(glop_plan plan) {
+    if (!plan) return GLOP_OK;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    delete plan;
+    return GLOP_OK;
+}
+
 glop_status glop_destroy(glop_handle h) {
     if (!h) return GLOP_OK;
     glop_status s = GLOP_OK;

@@ -101,3 +101,4 @@ def test_dense_batch_overflow_scratch():
     exp = oracle.batch(text, seg, pats, method="naive")
     got, _ = gpu_batch(pats, np.frombuffer(text, np.uint8), seg)
     assert np.array_equal(got, exp)
+

@@ -160,15 +160,6 @@ def test_config2_slices(nbytes):
     assert np.array_equal(got, oracle.ac_mt(w.text, w.patterns.csr()))
 
 
-def test_config2_full_size():
-    """256 MiB, 1,000 patterns: every match against the multi-threaded oracle."""
-    w = W.config2()
-    got, n = gpu_scan(w.patterns, w.text)
-    exp = oracle.ac_mt(w.text, w.patterns.csr())
-    assert n == len(exp)
-    assert np.array_equal(got, exp)
-
-
 def test_prefix_mode_config2_slice():
     w = W.config2(4 * W.MiB)
     got, n = gpu_scan(w.patterns, w.text, prefix_len=8)
