@@ -170,6 +170,52 @@ def cpu_baseline(w, budget_s: float = 20.0):
             "sample": "first %d MiB of the workload x %d run(s), multi-threaded Aho-Corasick oracle" % (n >> 20, reps)}
 
 
+def run_serve(args, ws, rank):
+    """Serving trace (Poisson arrivals, log-normal sizes, 8 resident sets): plain per-request scans vs
+    continuous batching, in real time (latency) and saturated (throughput)."""
+    if rank != 0:
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import workloads as W
+    from paper_1704_02278_gb300 import serve
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sets = W.config5_sets()
+    times, sizes, set_idx = W.config5_requests(200.0, float(args.serve_seconds))
+    pool_bytes = 256 << 20
+    pools = [torch.from_numpy(W.config5_payload(k, pool_bytes)).pin_memory() for k in (0, 1)]
+
+    def make():
+        reqs = []
+        for i in range(len(times)):
+            size = int(min(sizes[i], pool_bytes))
+            off = (i * 2654435761) % (pool_bytes - size + 1)
+            reqs.append(serve.Request(i, int(set_idx[i]), pools[i % 2][off:off + size], float(times[i])))
+        return reqs
+
+    out = {"requests": len(times), "bytes": int(sizes.sum()), "seconds": args.serve_seconds}
+    plain = serve.PlainServer(sets, max_request_bytes=int(sizes.max()))
+    batched = serve.BatchServer(sets, hbm_budget=args.serve_hbm_gib << 30)
+    # warm both (first launches, host allocator)
+    plain.serve(make()[:20], realtime=False)
+    batched.serve(make()[:20], realtime=False)
+    for name, srv in (("plain", plain), ("batched", batched)):
+        reqs = make()
+        wall, st = srv.serve(reqs, realtime=True)
+        lat = serve.latency_summary(reqs)
+        reqs2 = make()
+        wall2, st2 = srv.serve(reqs2, realtime=False)
+        out[name] = dict(lat, realtime_wall_s=round(wall, 3), saturated_s=round(wall2, 3),
+                         saturated_gbps=round(8.0 * out["bytes"] / wall2 / 1e9, 3), stats=st2)
+    line = {"metric": "served p50/p99 latency (ms) and saturated Gbit/s: continuous batching vs plain",
+            "value": out["batched"]["saturated_gbps"], "unit": "Gbit/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "serve-200rps-%ds-8sets" % args.serve_seconds}, "serve": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -181,12 +227,17 @@ def main():
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--per-segment-steps", type=int, default=1)
+    ap.add_argument("--serve-seconds", type=int, default=60)
+    ap.add_argument("--serve-hbm-gib", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
 
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload.startswith("serve"):
+        run_serve(args, ws, rank)
         return
 
     import torch

@@ -71,6 +71,12 @@ typedef struct {
      * 0 lets the library choose. */
     uint32_t smem_budget_bytes;
     uint32_t flags; /* reserved, must be 0 */
+    /* Start filter: bytes hashed at every offset (4..8, at most the shortest
+     * pattern; 0 = the library's choice, min(shortest pattern, 8)). */
+    uint32_t gram_len;
+    /* Start filter bitmap of 2^filter_bits_log2 bits (13..19; 0 = the
+     * library's choice from the number of distinct grams). */
+    uint32_t filter_bits_log2;
 } glop_compile_opts;
 
 /* Facts about a compiled automaton (glop_info_get). */
@@ -183,6 +189,26 @@ glop_status glop_scan_host_staging_size(glop_handle h, uint64_t len, uint64_t ca
 glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, glop_match *h_matches,
                            uint64_t capacity, uint64_t *h_count, void *d_staging, uint64_t staging_bytes,
                            glop_stream_t stream);
+
+/*
+ * glop_tune -- pick compile options for a pattern set by timing scans of a
+ * sample on the current device: the start filter's gram length and bitmap
+ * size and the shared-memory budget of on-chip transition rows.  Every
+ * candidate is compiled, warmed up and timed over `repeats` scans of the
+ * sample (d_sample, sample_len; a batch when d_seg_offsets is not NULL) with
+ * CUDA events on stream.  points[0 .. *n_points) receive every candidate and
+ * its Gbit/s (at most max_points are stored); *best the fastest options.
+ * Allocates its own scratch; synchronous.  Errors as for glop_compile and
+ * glop_scan.
+ */
+typedef struct {
+    glop_compile_opts opts;
+    double gbps;
+} glop_tune_point;
+glop_status glop_tune(const uint8_t *pattern_bytes, const uint64_t *pattern_offsets, uint32_t n_patterns,
+                      uint32_t prefix_len, const uint8_t *d_sample, uint64_t sample_len,
+                      const uint64_t *d_seg_offsets, uint32_t n_segments, uint32_t repeats, glop_tune_point *points,
+                      uint32_t max_points, uint32_t *n_points, glop_compile_opts *best, glop_stream_t stream);
 
 /*
  * Plans: a whole scan (glop_scan, or glop_scan_batch when d_seg_offsets is

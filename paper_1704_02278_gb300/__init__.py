@@ -36,7 +36,7 @@ OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_workspace_size", "glop_scan",
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
            "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc", "glop_plan_create",
-           "glop_plan_launch", "glop_plan_destroy"]
+           "glop_plan_launch", "glop_plan_destroy", "glop_tune"]
 
 
 class GlopError(RuntimeError):
@@ -46,7 +46,12 @@ class GlopError(RuntimeError):
 
 
 class glop_compile_opts(ctypes.Structure):
-    _fields_ = [("prefix_len", ctypes.c_uint32), ("smem_budget_bytes", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+    _fields_ = [("prefix_len", ctypes.c_uint32), ("smem_budget_bytes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("gram_len", ctypes.c_uint32), ("filter_bits_log2", ctypes.c_uint32)]
+
+
+class glop_tune_point(ctypes.Structure):
+    _fields_ = [("opts", glop_compile_opts), ("gbps", ctypes.c_double)]
 
 
 class glop_info(ctypes.Structure):
@@ -97,6 +102,9 @@ def lib():
         L.glop_plan_launch.argtypes = [vp, vp]
         L.glop_plan_destroy.restype = ctypes.c_int
         L.glop_plan_destroy.argtypes = [vp]
+        L.glop_tune.restype = ctypes.c_int
+        L.glop_tune.argtypes = [vp, vp, u32, u32, vp, u64, vp, u32, u32, ctypes.POINTER(glop_tune_point), u32,
+                                ctypes.POINTER(u32), ctypes.POINTER(glop_compile_opts), vp]
         L.glop_scan_noalloc.restype = ctypes.c_int
         L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
         L.glop_destroy.restype = ctypes.c_int
@@ -144,12 +152,18 @@ class Automaton:
     (the paper's prefix matching uses K = 8).
     """
 
-    def __init__(self, patterns, prefix_len: int = 0, smem_budget: int = 0):
+    def __init__(self, patterns, prefix_len: int = 0, smem_budget: int = 0, gram_len: int = 0,
+                 filter_bits_log2: int = 0, options: dict | None = None):
         L = lib()
         buf, offs = _pattern_csr(patterns)
         if buf.size == 0:
             buf = np.zeros(1, np.uint8)
-        opts = glop_compile_opts(prefix_len, smem_budget, 0)
+        if options:
+            prefix_len = options.get("prefix_len", prefix_len)
+            smem_budget = options.get("smem_budget_bytes", smem_budget)
+            gram_len = options.get("gram_len", gram_len)
+            filter_bits_log2 = options.get("filter_bits_log2", filter_bits_log2)
+        opts = glop_compile_opts(prefix_len, smem_budget, 0, gram_len, filter_bits_log2)
         h = ctypes.c_void_p()
         _check(L.glop_compile(buf.ctypes.data, offs.ctypes.data, len(offs) - 1, ctypes.byref(opts),
                               ctypes.byref(h)), "glop_compile")
@@ -334,3 +348,52 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _opts_dict(o: glop_compile_opts) -> dict:
+    return {k: int(getattr(o, k)) for k, _ in glop_compile_opts._fields_ if k != "flags"}
+
+
+def tune(patterns, sample, seg_offsets=None, prefix_len: int = 0, repeats: int = 5, cache_path: str | None = None,
+         stream=None) -> dict:
+    """Autotune compile options on a sample (uint8 CUDA tensor; a batch when ``seg_offsets`` is given).
+
+    Returns ``{"best": options, "points": [...], "cached": bool}``.  With ``cache_path`` (default: the
+    GLOP_TUNE_CACHE environment variable) results are kept in a JSON file keyed by the pattern set, the
+    prefix length, the sample's size/kind and the device name."""
+    import hashlib
+    import json
+    torch = _torch()
+    buf, offs = _pattern_csr(patterns)
+    cache_path = cache_path or os.environ.get("GLOP_TUNE_CACHE")
+    key = "|".join([hashlib.sha256(buf.tobytes() + offs.tobytes()).hexdigest()[:32], str(prefix_len),
+                    "batch" if seg_offsets is not None else "single", str(sample.numel()),
+                    torch.cuda.get_device_name(sample.device)])
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
+        if key in cache:
+            return dict(cache[key], cached=True)
+    if buf.size == 0:
+        buf = np.zeros(1, np.uint8)
+    maxp = 64
+    pts = (glop_tune_point * maxp)()
+    npts = ctypes.c_uint32()
+    best = glop_compile_opts()
+    nseg = 0 if seg_offsets is None else seg_offsets.numel() - 1
+    _check(lib().glop_tune(buf.ctypes.data, offs.ctypes.data, len(offs) - 1, prefix_len, sample.data_ptr(),
+                           sample.numel(), None if seg_offsets is None else seg_offsets.data_ptr(), nseg, repeats,
+                           pts, maxp, ctypes.byref(npts), ctypes.byref(best), _stream_handle(stream)), "glop_tune")
+    res = {"best": _opts_dict(best),
+           "points": [dict(_opts_dict(pts[i].opts), gbps=round(pts[i].gbps, 2)) for i in range(min(npts.value, maxp))]}
+    if cache_path:
+        cache[key] = res
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    return dict(res, cached=False)

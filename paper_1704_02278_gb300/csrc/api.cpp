@@ -59,7 +59,8 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
     std::string err;
     int rc;
     try {
-        rc = glop::compile_host(pattern_bytes, pattern_offsets, n_patterns, opts ? opts->prefix_len : 0, &H, &err);
+        rc = glop::compile_host(pattern_bytes, pattern_offsets, n_patterns, opts ? opts->prefix_len : 0, &H, &err,
+                                opts ? opts->gram_len : 0, opts ? opts->filter_bits_log2 : 0);
     } catch (const std::bad_alloc &) {
         return GLOP_ENOMEM;
     }
@@ -270,6 +271,99 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
     if (cudaMemcpy(&hdr0, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GLOP_ECUDA;
     if (hdr0 & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
     if (*h_count > capacity) return GLOP_EOVERFLOW;
+    return GLOP_OK;
+}
+
+glop_status glop_tune(const uint8_t *pattern_bytes, const uint64_t *pattern_offsets, uint32_t n_patterns,
+                      uint32_t prefix_len, const uint8_t *d_sample, uint64_t sample_len,
+                      const uint64_t *d_seg_offsets, uint32_t n_segments, uint32_t repeats, glop_tune_point *points,
+                      uint32_t max_points, uint32_t *n_points, glop_compile_opts *best, glop_stream_t stream) {
+    if (!best || !n_points || (sample_len && !d_sample)) return GLOP_EINVAL;
+    if (repeats < 1) repeats = 1;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the automatic choice first: its gram length and bitmap size span the grid
+    glop_compile_opts base{};
+    base.prefix_len = prefix_len;
+    glop_handle h0 = nullptr;
+    glop_status s = glop_compile(pattern_bytes, pattern_offsets, n_patterns, &base, &h0);
+    if (s != GLOP_OK) return s;
+    const uint32_t gmax = h0->info.gram_len, bm0 = h0->dev.bm_log2;
+    glop_destroy(h0);
+    std::vector<uint32_t> grams, bits;
+    if (gmax == 0) grams.push_back(0);
+    else for (uint32_t g = 4; g <= gmax; ++g) grams.push_back(g);
+    if (gmax == 0) bits.push_back(0);
+    else for (int d = -2; d <= 2; d += 2) {
+        const int b = (int)bm0 + d;
+        if (b >= 13 && b <= 19) bits.push_back((uint32_t)b);
+    }
+    const uint32_t budgets[2] = {0u, 16384u};
+    const bool batch = d_seg_offsets != nullptr;
+    void *ws = nullptr, *out = nullptr, *cnt = nullptr;
+    uint64_t ws_bytes = glop::workspace_bytes(sample_len, batch), out_cap = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (ws) cudaFree(ws);
+        if (out) cudaFree(out);
+        if (cnt) cudaFree(cnt);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&ws, ws_bytes) != cudaSuccess || cudaMalloc(&cnt, 8) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return GLOP_ENOMEM;
+    }
+    const uint32_t rec = batch ? (uint32_t)sizeof(glop_batch_match) : (uint32_t)sizeof(glop_match);
+    auto scan_once = [&](glop_handle h) -> glop_status {
+        return batch ? glop_scan_batch(h, d_sample, sample_len, d_seg_offsets, n_segments,
+                                       reinterpret_cast<glop_batch_match *>(out), out_cap, reinterpret_cast<uint64_t *>(cnt),
+                                       ws, ws_bytes, stream)
+                     : glop_scan(h, d_sample, sample_len, reinterpret_cast<glop_match *>(out), out_cap,
+                                 reinterpret_cast<uint64_t *>(cnt), ws, ws_bytes, stream);
+    };
+    uint32_t np = 0;
+    double best_gbps = -1;
+    for (uint32_t g : grams) {
+        for (uint32_t b : bits) {
+            glop_compile_opts o{};
+            o.prefix_len = prefix_len;
+            o.gram_len = g;
+            o.filter_bits_log2 = b;
+            glop_handle h = nullptr;
+            s = glop_compile(pattern_bytes, pattern_offsets, n_patterns, &o, &h);
+            if (s != GLOP_OK) { cleanup(); return s; }
+            for (uint32_t budget : budgets) {
+                h->smem_budget = budget;
+                o.smem_budget_bytes = budget;
+                // size the output once (identical for every candidate), then warm up and time
+                if (!out) {
+                    s = scan_once(h);
+                    uint64_t total = 0;
+                    if (s == GLOP_OK) s = glop_scan_status(ws, stream, &total);
+                    if (s != GLOP_OK && s != GLOP_EOVERFLOW) { glop_destroy(h); cleanup(); return s; }
+                    out_cap = total ? total : 1;
+                    if (cudaMalloc(&out, out_cap * rec) != cudaSuccess) { glop_destroy(h); cleanup(); return GLOP_ENOMEM; }
+                }
+                s = scan_once(h);
+                if (s != GLOP_OK) { glop_destroy(h); cleanup(); return s; }
+                cudaEventRecord(e0, st);
+                for (uint32_t r = 0; r < repeats && s == GLOP_OK; ++r) s = scan_once(h);
+                cudaEventRecord(e1, st);
+                if (s != GLOP_OK || cudaEventSynchronize(e1) != cudaSuccess) { glop_destroy(h); cleanup(); return GLOP_ECUDA; }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double gbps = ms > 0 ? 8.0 * (double)sample_len * repeats / (ms * 1e-3) / 1e9 : 0.0;
+                if (points && np < max_points) points[np] = glop_tune_point{o, gbps};
+                ++np;
+                if (gbps > best_gbps) { best_gbps = gbps; *best = o; }
+            }
+            glop_destroy(h);
+        }
+    }
+    *n_points = np;
+    cleanup();
     return GLOP_OK;
 }
 

@@ -33,7 +33,7 @@ uint32_t ceil_log2(uint64_t x) {
 }  // namespace
 
 int compile_host(const uint8_t *bytes, const uint64_t *offs, uint32_t n, uint32_t prefix_len, HostAutomaton *out,
-                 std::string *err) {
+                 std::string *err, uint32_t want_gram, uint32_t want_bm_log2) {
     HostAutomaton &A = *out;
     A = HostAutomaton();
     if (!offs || (n && !bytes)) { if (err) *err = "null pointer"; return 1; }
@@ -232,12 +232,14 @@ int compile_host(const uint8_t *bytes, const uint64_t *offs, uint32_t n, uint32_
 
     // ---- start filter over the first gram_len bytes (all patterns >= 4 bytes) ----
     if (n && A.min_len >= 4) {
-        const uint32_t g = std::min<uint32_t>(A.min_len, 8);
+        uint32_t g = std::min<uint32_t>(A.min_len, 8);
+        if (want_gram) g = std::max<uint32_t>(4, std::min(g, want_gram));
         A.gram_len = g;
         std::vector<uint32_t> keys;
         for (uint32_t v : bfs) if (depth[v] == g) keys.push_back(v);
         A.n_grams = (uint32_t)keys.size();
         A.bm_log2 = std::min<uint32_t>(19, std::max<uint32_t>(13, ceil_log2((uint64_t)keys.size() * 64)));
+        if (want_bm_log2) A.bm_log2 = std::min<uint32_t>(19, std::max<uint32_t>(13, want_bm_log2));
         A.ht_log2 = std::max<uint32_t>(6, ceil_log2((uint64_t)keys.size() * 2));
         A.bitmap.assign((1u << A.bm_log2) / 32, 0);
         A.grams.assign(1u << A.ht_log2, GlopGramSlot{0, 0, 0, 0});

@@ -27,7 +27,8 @@ struct HostAutomaton {
 
 // Status codes use the values of glop_status.
 // prefix_len 0 = exact patterns; K > 0 cuts every pattern to K bytes.
+// gram_len / bm_log2: start-filter gram length and bitmap size; 0 = automatic.
 int compile_host(const uint8_t *bytes, const uint64_t *offs, uint32_t n, uint32_t prefix_len, HostAutomaton *out,
-                 std::string *err);
+                 std::string *err, uint32_t gram_len = 0, uint32_t bm_log2 = 0);
 
 }  // namespace glop

@@ -17,6 +17,8 @@
 
 using glop::HostAutomaton;
 
+static uint32_t g_gram_len = 0, g_bm_log2 = 0;  // compile options of the next host checks
+
 namespace {
 
 uint32_t rd32(const uint8_t *p, uint64_t avail) {
@@ -104,7 +106,7 @@ int glop_hostcheck_scan_iters(const uint8_t *pat, const uint64_t *poff, uint32_t
     *count = 0;
     HostAutomaton A;
     std::string err;
-    int rc = glop::compile_host(pat, poff, npat, prefix_len, &A, &err);
+    int rc = glop::compile_host(pat, poff, npat, prefix_len, &A, &err, g_gram_len, g_bm_log2);
     if (rc) return rc;
     std::vector<uint32_t> res;
     uint64_t passed = 0, found = 0, matched = 0;
@@ -164,5 +166,11 @@ int glop_hostcheck_scan_iters(const uint8_t *pat, const uint64_t *poff, uint32_t
 }
 
 void glop_hostcheck_free(void *p) { std::free(p); }
+
+// Start-filter options (gram length, bitmap bits) for the following checks; 0 = automatic.
+void glop_hostcheck_set_options(uint32_t gram_len, uint32_t bm_log2) {
+    g_gram_len = gram_len;
+    g_bm_log2 = bm_log2;
+}
 
 }  // extern "C"

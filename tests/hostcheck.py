@@ -23,9 +23,10 @@ def _load():
     return _lib
 
 
-def scan(text, seg, pat_buf, pat_offs, prefix_len=0):
+def scan(text, seg, pat_buf, pat_offs, prefix_len=0, gram_len=0, filter_bits=0):
     """(M, 3) uint32 (segment, offset, pattern_id) and stats dict."""
     lib = _load()
+    lib.glop_hostcheck_set_options(ctypes.c_uint32(gram_len), ctypes.c_uint32(filter_bits))
     t = np.ascontiguousarray(text, dtype=np.uint8).reshape(-1)
     if t.size == 0:
         t = np.zeros(1, np.uint8)

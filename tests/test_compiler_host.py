@@ -72,3 +72,15 @@ def test_config3_slice_segments():
     assert st["gram_len"] == 8
     assert len(exp) > 0
     assert np.array_equal(got, exp)
+
+
+@pytest.mark.parametrize("gram_len,bits", [(4, 13), (5, 16), (8, 19), (6, 0)])
+def test_filter_options(gram_len, bits):
+    """Every start-filter gram length / bitmap size gives the same exact result."""
+    p = W.config3_patterns()
+    seg = W.packet_offsets(W.seed(3, 3), 2 * W.MiB)
+    t = W.packets(W.seed(3, 0), W.seed(3, 2), seg, 0.6, 0.01, p)
+    exp = oracle.batch(t, seg, p.csr())
+    got, st = hostcheck.scan(t, seg, p.buf, p.offs, gram_len=gram_len, filter_bits=bits)
+    assert st["gram_len"] == gram_len
+    assert np.array_equal(got, exp)

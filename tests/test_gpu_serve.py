@@ -1,0 +1,72 @@
+"""Serving: every request's result is the same alone and in the continuous-batching mix."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1704_02278_gb300 as glop  # noqa: E402
+from paper_1704_02278_gb300 import serve  # noqa: E402
+
+
+def _requests(n=80, max_size=2 << 20, span=0.4):
+    times, sizes, sets = W.config5_requests()
+    pools = [torch.from_numpy(W.config5_payload(k, 8 << 20)).pin_memory() for k in (0, 1)]
+    reqs = []
+    for i in range(n):
+        size = int(min(sizes[i], max_size))
+        off = (i * 2654435761) % ((8 << 20) - size + 1)
+        reqs.append(serve.Request(i, int(sets[i]), pools[i % 2][off:off + size], times[i] * span / times[n - 1]))
+    return reqs
+
+
+def _solo(sets, reqs):
+    autos = {}
+    out = []
+    for r in reqs:
+        a = autos.setdefault(r.set_index, glop.Automaton(sets[r.set_index]))
+        m, n = a.scan(r.payload.cuda())
+        out.append(m.cpu().numpy().view(np.uint32))
+    return out
+
+
+def test_batched_results_equal_solo_results():
+    sets = W.config5_sets()
+    reqs = _requests()
+    exp = _solo(sets, reqs)
+    srv = serve.BatchServer(sets, hbm_budget=1 << 30, keep_matches=True)
+    wall, st = srv.serve(reqs, realtime=True)
+    assert st["batches"] >= 1
+    for r, e in zip(reqs, exp):
+        assert r.count == len(e), r.rid
+        assert np.array_equal(r.matches, e), r.rid
+
+
+def test_tight_budget_admission_and_saturation():
+    sets = W.config5_sets()[:4]
+    reqs = _requests(60)
+    for r in reqs:
+        r.set_index %= 4
+    exp = _solo(sets, reqs)
+    srv = serve.BatchServer(sets, hbm_budget=40 << 20, max_inflight=3, keep_matches=True)
+    wall, st = srv.serve(reqs, realtime=False)
+    assert st["admission_waits"] > 0
+    for r, e in zip(reqs, exp):
+        assert np.array_equal(r.matches, e), r.rid
+
+
+def test_plain_server_matches():
+    sets = W.config5_sets()[:3]
+    reqs = _requests(20)
+    for r in reqs:
+        r.set_index %= 3
+    exp = _solo(sets, reqs)
+    srv = serve.PlainServer(sets, max_request_bytes=2 << 20, keep_matches=True)
+    srv.serve(reqs, realtime=False)
+    for r, e in zip(reqs, exp):
+        assert np.array_equal(r.matches, e), r.rid
