@@ -36,6 +36,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "glop_hash.h"
@@ -95,6 +96,7 @@ struct KParams {
     uint32_t halo, slot_bytes, hot_n, grams_in_smem, aligned;
     uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring, off_q;
     long long spin_budget;
+    uint32_t barrier_extra;  // fault injection for tests: grid barriers wait for this many absent blocks
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -797,7 +799,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
 
     // ================= phase B =================
     const uint32_t G = gridDim.x;
-    grid_sync(p.hdr + 8, G, p.spin_budget, p.hdr);
+    grid_sync(p.hdr + 8, G + p.barrier_extra, p.spin_budget, p.hdr);
     const uint64_t R = (p.n_sub + G - 1) / G;
     const uint64_t ra = min(p.n_sub, (uint64_t)blockIdx.x * R), rb = min(p.n_sub, ra + R);
     {
@@ -812,7 +814,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             if (lane == 0) p.sums[blockIdx.x] = v;
         }
     }
-    grid_sync(p.hdr + 9, G, p.spin_budget, p.hdr);
+    grid_sync(p.hdr + 9, G + p.barrier_extra, p.spin_budget, p.hdr);
     if (warp == 0) {
         unsigned long long before = 0, all = 0;
         for (uint32_t c = lane; c < G; c += 32) {
@@ -1023,6 +1025,11 @@ int launch_scan(const ScanLaunch &L) {
     kp.slot_bytes = align_up(CHUNK + halo + 64, 128);
     kp.aligned = (reinterpret_cast<uintptr_t>(L.text) & 15) == 0;
     kp.spin_budget = 4000000000ll;  // about 2 s of SM clock
+    // Failure-detection tests make a bounded wait run out on purpose: GLOP_TEST_BARRIER_EXTRA=k makes the
+    // grid barriers wait for k blocks that do not exist, GLOP_TEST_SPIN_BUDGET shortens every wait (cycles).
+    kp.barrier_extra = 0;
+    if (const char *e = std::getenv("GLOP_TEST_BARRIER_EXTRA")) kp.barrier_extra = (uint32_t)std::strtoul(e, nullptr, 10);
+    if (const char *e = std::getenv("GLOP_TEST_SPIN_BUDGET")) kp.spin_budget = std::strtoll(e, nullptr, 10);
 
     // shared memory: class map, bitmap, gram table, block state, ring, hot rows
     const uint32_t budget = (uint32_t)pr.smem_optin;
