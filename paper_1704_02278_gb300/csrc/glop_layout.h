@@ -64,6 +64,6 @@ struct GlopDevAutomaton {
     const uint32_t *cum_off;       // [n_states + 1] output list of each state
     const uint32_t *cum_ids;       // pattern ids, ascending within a list
     uint32_t n_cum_ids;            // entries of cum_ids
-    const uint32_t *bitmap;        // [(1 << bm_log2) / 32]
+    const uint32_t *bitmap;        // [(1 << bm_log2) / 32]; index i is bit (31 - i % 32) of word i / 32
     const GlopGramSlot *grams;     // [1 << ht_log2]
 };

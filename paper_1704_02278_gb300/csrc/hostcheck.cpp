@@ -124,7 +124,7 @@ int glop_hostcheck_scan_iters(const uint8_t *pat, const uint64_t *poff, uint32_t
                 uint32_t h = glop_gram_hash(w0, w1);
                 uint32_t bi = glop_bitmap_index(h, A.bm_log2);
                 if (iters) iters[i] = 255;
-                if (!((A.bitmap[bi >> 5] >> (bi & 31)) & 1u)) continue;
+                if (!((A.bitmap[bi >> 5] << (bi & 31)) & 0x80000000u)) continue;
                 if (iters) iters[i] = 0;
                 ++passed;
                 uint32_t m = (1u << A.ht_log2) - 1, slot = glop_table_slot(h, A.ht_log2), v = 0;

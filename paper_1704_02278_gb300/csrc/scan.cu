@@ -58,7 +58,9 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr unsigned long long END_TICKET = ~0ull;
 constexpr uint32_t REC_OVERFLOW = 0xFFFFFFFFu;
 constexpr uint32_t QCAP = 128;   // survivors per walk batch of one warp
-constexpr uint32_t QBYTES = QCAP * 10;  // per-warp queue: offsets (u16), states (u32), walk bounds (u32)
+constexpr uint32_t CCAP = 64;    // walks listed for continuation after their first step
+// per-warp queue: offsets (u16), states (u32), walk bounds (u32); continuation states (u32), positions (u32), indexes (u8)
+constexpr uint32_t QBYTES = QCAP * 10 + CCAP * 9;
 
 struct SubDesc {
     uint32_t rec_start, n_rec;  // absolute record index; n_rec == REC_OVERFLOW: records not stored
@@ -230,8 +232,9 @@ struct TextView {
 #endif
 };
 
+template <bool DEEP = true>
 __device__ __forceinline__ uint32_t tbyte(const TextView &v, uint32_t pos) {
-    if (pos < v.n_stage) return v.buf[pos];
+    if (!DEEP || pos < v.n_stage) return v.buf[pos];
     uint32_t r = 0;
     GLOP_CK(v.hdr, pos < v.avail, 20, pos) r = __ldg(v.gtext + pos);
     return r;
@@ -243,6 +246,8 @@ __device__ __forceinline__ uint32_t tword(const uint32_t *b32, uint32_t pos) {
     return __funnelshift_r(b32[a], b32[a + 1], 8 * (pos & 3));
 }
 
+// Raw dense-row entry of state s for class cl: uint16 (state | 0x8000 when
+// terminal) or int32 (state | GLOP_TERM); 0 when there is no transition.
 template <bool ROW16>
 __device__ __forceinline__ uint32_t row_entry(const GlopDevAutomaton &A, const void *rows_s, uint32_t hot_n,
                                               uint32_t s, uint32_t cl, uint32_t *hdr) {
@@ -250,71 +255,80 @@ __device__ __forceinline__ uint32_t row_entry(const GlopDevAutomaton &A, const v
     (void)hdr;
     GLOP_BAIL(hdr, s < A.n_dense && cl < C, 21, s, 0u)
     const uint32_t r = s - A.hot_lo;
-    if (ROW16) {
-        const uint32_t e = (r < hot_n)
-                               ? (uint32_t)reinterpret_cast<const uint16_t *>(rows_s)[r * C + cl]
-                               : (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(A.rows) + (size_t)s * C + cl);
-        return (e & 0x7FFFu) | ((e & 0x8000u) << 16);
-    }
+    if (ROW16)
+        return (r < hot_n) ? (uint32_t)reinterpret_cast<const uint16_t *>(rows_s)[r * C + cl]
+                           : (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(A.rows) + (size_t)s * C + cl);
     return (r < hot_n) ? (uint32_t)reinterpret_cast<const int32_t *>(rows_s)[r * C + cl]
                        : (uint32_t)__ldg(reinterpret_cast<const int32_t *>(A.rows) + (size_t)s * C + cl);
 }
 
+// One dense-row transition; returns true when the walk is over.
+template <bool ROW16, bool DEEP>
+__device__ __forceinline__ bool dense_step(const GlopDevAutomaton &A, const uint8_t *cls_s, const void *rows_s,
+                                           uint32_t hot_n, const TextView &v, uint32_t &s, uint32_t &pos,
+                                           uint32_t end, uint32_t &t, uint32_t *hdr) {
+    if (pos >= end) return true;
+    const uint32_t e = row_entry<ROW16>(A, rows_s, hot_n, s, cls_s[tbyte<DEEP>(v, pos)], hdr);
+    if (!e) return true;
+    constexpr uint32_t TB = ROW16 ? 0x8000u : GLOP_TERM;
+    s = e & (TB - 1u);
+    ++pos;
+    if (e & TB) t = s;
+    return false;
+}
+
 // One step of a walk from state s with the next text byte at sub-tile
-// position pos, never reading at or past end: a dense-row transition or one
-// chain piece.  t is the deepest terminal state passed so far.  Returns true
-// when the walk is over (t is then final).
-template <bool ROW16>
+// position pos, never reading at or past end: a dense-row transition when s
+// is dense, then one chain piece (up to 16 bytes compared at once) when the
+// walk is on a chain, then one more dense transition when the piece exits
+// into a dense state.  t is the deepest terminal state passed so far.
+// Returns true when the walk is over (t is then final).
+template <bool ROW16, bool DEEP>
 __device__ __forceinline__ bool step(const GlopDevAutomaton &A, const uint8_t *cls_s, const void *rows_s,
                                      uint32_t hot_n, const TextView &v, uint32_t &s, uint32_t &pos, uint32_t end,
                                      uint32_t &t, uint32_t *hdr) {
+#ifdef GLOP_BOUNDS_CHECK
     if (s >= A.n_states) {
         fail_check(hdr, 1, s);
         t = 0;
         return true;
     }
-    if (s < A.n_dense) {
-        if (pos >= end) return true;
-        const uint32_t e = row_entry<ROW16>(A, rows_s, hot_n, s, cls_s[tbyte(v, pos)], hdr);
-        if (!e) return true;
-        s = e & GLOP_STATE_MASK;
-        ++pos;
-        if (e & GLOP_TERM) t = s;
-        return false;
-    }
+#endif
+    if (s < A.n_dense && dense_step<ROW16, DEEP>(A, cls_s, rows_s, hot_n, v, s, pos, end, t, hdr)) return true;
+    if (s < A.n_dense) return false;
     const uint4 *rec = reinterpret_cast<const uint4 *>(A.chain) + 2 * (size_t)(s - A.n_dense);
     const uint4 c0 = __ldg(rec), c1 = __ldg(rec + 1);
     const uint32_t exitv = c1.x, term = c1.y, tm = c1.z & 0xFFFFu, rem = (c1.z >> 16) & 0xFFu, nst = c1.z >> 24;
     const uint32_t lim = min(rem, end - pos);
     uint32_t m;
     if (pos + 20 <= v.n_stage) {
-        const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf);
-        const uint32_t x0 = tword(b32, pos) ^ c0.x, x1 = tword(b32, pos + 4) ^ c0.y, x2 = tword(b32, pos + 8) ^ c0.z,
-                       x3 = tword(b32, pos + 12) ^ c0.w;
-        m = 16u;
-        if (x3) m = 12 + ((uint32_t)(__ffs(x3) - 1) >> 3);
-        if (x2) m = 8 + ((uint32_t)(__ffs(x2) - 1) >> 3);
-        if (x1) m = 4 + ((uint32_t)(__ffs(x1) - 1) >> 3);
-        if (x0) m = (uint32_t)(__ffs(x0) - 1) >> 3;
+        const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf) + (pos >> 2);
+        const uint32_t sh = 8 * (pos & 3);
+        const uint32_t y0 = b32[0], y1 = b32[1], y2 = b32[2], y3 = b32[3], y4 = b32[4];
+        const unsigned long long x01 = ((unsigned long long)(__funnelshift_r(y1, y2, sh) ^ c0.y) << 32) |
+                                       (__funnelshift_r(y0, y1, sh) ^ c0.x);
+        const unsigned long long x23 = ((unsigned long long)(__funnelshift_r(y3, y4, sh) ^ c0.w) << 32) |
+                                       (__funnelshift_r(y2, y3, sh) ^ c0.z);
+        m = x01 ? (uint32_t)(__ffsll((long long)x01) - 1) >> 3
+                : x23 ? 8 + ((uint32_t)(__ffsll((long long)x23) - 1) >> 3) : 16u;
         m = min(m, lim);
     } else {
         m = 0;
         while (m < lim) {
             const uint32_t w = m < 4 ? c0.x : m < 8 ? c0.y : m < 12 ? c0.z : c0.w;
-            if (tbyte(v, pos + m) != ((w >> (8 * (m & 3))) & 0xFFu)) break;
+            if (tbyte<DEEP>(v, pos + m) != ((w >> (8 * (m & 3))) & 0xFFu)) break;
             ++m;
         }
     }
     const uint32_t hit = tm & ((2u << min(m, nst)) - 1u);
     if (hit) t = s + 31 - __clz(hit);
     else if (term) t = term;
-    if (exitv && m == rem) {
-        s = exitv & GLOP_STATE_MASK;
-        pos += m;
-        if (exitv & GLOP_TERM) t = s;
-        return false;
-    }
-    return true;
+    if (!exitv || m != rem) return true;
+    s = exitv & GLOP_STATE_MASK;
+    pos += m;
+    if (exitv & GLOP_TERM) t = s;
+    if (s < A.n_dense) return dense_step<ROW16, DEEP>(A, cls_s, rows_s, hot_n, v, s, pos, end, t, hdr);
+    return false;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -347,7 +361,7 @@ __global__ void init_kernel(uint32_t *hdr, uint32_t *tile_seg, uint64_t n_sub, c
     }
 }
 
-template <int FILT, bool BATCH, bool ROW16>
+template <int FILT, bool BATCH, bool ROW16, bool DEEP>
 __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const GlopDevAutomaton &A = p.A;
@@ -357,8 +371,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     uint8_t *cls_s = smem;
     uint32_t *fb_s = reinterpret_cast<uint32_t *>(smem + 256);
     const uint32_t *bm_s = reinterpret_cast<const uint32_t *>(smem + p.off_bitmap);
+    // 4-byte grams: the shared-memory copy keeps (key_lo, val) only, 8 bytes a slot
     const GlopGramSlot *grams =
         p.grams_in_smem ? reinterpret_cast<const GlopGramSlot *>(smem + p.off_grams) : A.grams;
+    const uint2 *grams8 = reinterpret_cast<const uint2 *>(smem + p.off_grams);
     const void *rows_s =
         smem + p.off_rows + (((size_t)A.hot_lo * A.n_classes * (ROW16 ? 2u : 4u)) & 15);
     CtaMisc *mc = reinterpret_cast<CtaMisc *>(smem + p.off_misc);
@@ -374,8 +390,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             for (uint32_t i = tid; i < (1u << A.bm_log2) / 128; i += THREADS) dst[i] = __ldg(src + i);
             if (p.grams_in_smem) {
                 const uint4 *gs = reinterpret_cast<const uint4 *>(A.grams);
-                uint4 *gd = reinterpret_cast<uint4 *>(smem + p.off_grams);
-                for (uint32_t i = tid; i < (1u << A.ht_log2); i += THREADS) gd[i] = __ldg(gs + i);
+                if (FILT == 4) {
+                    uint2 *gd = reinterpret_cast<uint2 *>(smem + p.off_grams);
+                    for (uint32_t i = tid; i < (1u << A.ht_log2); i += THREADS) {
+                        const uint4 e = __ldg(gs + i);
+                        gd[i] = make_uint2(e.x, e.z);
+                    }
+                } else {
+                    uint4 *gd = reinterpret_cast<uint4 *>(smem + p.off_grams);
+                    for (uint32_t i = tid; i < (1u << A.ht_log2); i += THREADS) gd[i] = __ldg(gs + i);
+                }
             }
         }
         // hot rows: copied in 16-byte units from the 16-byte boundary at or before their start
@@ -434,6 +458,14 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             uint32_t h = w0 * GLOP_HASH_M0;
             if (FILT == 8) h ^= w1 * GLOP_HASH_M1;
             uint32_t slot = glop_table_slot(h, A.ht_log2);
+            if (FILT == 4 && p.grams_in_smem) {
+                while (true) {
+                    const uint2 e = grams8[slot];
+                    if (!e.y) return 0u;
+                    if (e.x == w0) return e.y;
+                    slot = (slot + 1) & htmask;
+                }
+            }
             while (true) {
                 const uint4 e = *reinterpret_cast<const uint4 *>(grams + slot);
                 if (!e.z) return 0u;
@@ -466,22 +498,27 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 x[k] = w;
             }
         }
-        uint32_t mask = 0;
+        // Offsets are tested from the last to the first; each test rotates its
+        // bitmap word so the tested bit (stored bit-reversed) is bit 31 and
+        // shifts it into the mask, so offset j ends at bit j.
+        uint32_t acc[2] = {0u, 0u};
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            uint32_t bit;
+        for (int j = 31; j >= 0; --j) {
+            uint32_t rot;
             if (FILT) {
                 uint32_t h = __funnelshift_r(x[j >> 2], x[(j >> 2) + 1], 8 * (j & 3)) * GLOP_HASH_M0;
                 if (FILT == 8)
                     h ^= (__funnelshift_r(x[(j >> 2) + 1], x[(j >> 2) + 2], 8 * (j & 3)) & w1mask) * GLOP_HASH_M1;
                 const uint32_t bi = h >> bsh;
-                bit = (bm_s[bi >> 5] >> (bi & 31)) & 1u;
+                const uint32_t word = bm_s[bi >> 5];
+                rot = __funnelshift_l(word, word, bi);
             } else {
                 const uint32_t by = (x[j >> 2] >> (8 * (j & 3))) & 0xFFu;
-                bit = (fb_s[by >> 5] >> (by & 31)) & 1u;
+                rot = fb_s[by >> 5] << (31 - (by & 31));
             }
-            mask |= bit << j;
+            acc[j >> 4] = __funnelshift_l(rot, acc[j >> 4], 1);
         }
+        uint32_t mask = (acc[1] << 16) | acc[0];
         if (o + 32 > sub_len) mask &= (o >= sub_len) ? 0u : ((1u << (sub_len - o)) - 1u);
         return mask;
     };
@@ -641,30 +678,75 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 nw += __popc(bm);
             }
             __syncwarp();
-            // (3) walk pass: lanes refill from the queue as their walks end
-            {
+            // (3) walk pass.  (3a) every walk takes its first step in
+            // lock-step rounds of 32; the walks that go on are listed
+            // (state, position, queue index) and (3b) walked by lanes that
+            // refill from that list as their walks end.  qst[i] holds the
+            // deepest terminal state of walk i so far.
+            uint32_t *cst = reinterpret_cast<uint32_t *>(qbase + QCAP * 10);
+            uint32_t *cpos = cst + CCAP;
+            uint8_t *cidx = reinterpret_cast<uint8_t *>(cpos + CCAP);
+            auto run_cont = [&](uint32_t ncont) {
                 uint32_t nxt = 0, qi = 0, st = 0, pos = 0, t = 0, endw = endsub;
                 bool have = false;
                 while (true) {
                     const uint32_t wm = __ballot_sync(FULL, !have);
                     if (!have) {
-                        qi = nxt + __popc(wm & lt);
-                        if (qi < nw) {
-                            const uint32_t val = qst[qi];
-                            st = val & GLOP_STATE_MASK;
-                            t = (val & GLOP_TERM) ? st : 0u;
-                            pos = qoff[qi] + g;
+                        const uint32_t k = nxt + __popc(wm & lt);
+                        if (k < ncont) {
+                            qi = cidx[k];
+                            st = cst[k];
+                            pos = cpos[k];
+                            t = qst[qi];
                             if (BATCH) endw = qend[qi];
                             have = true;
                         }
                     }
                     nxt += __popc(wm);
                     if (!__any_sync(FULL, have)) break;
-                    if (have && step<ROW16>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr)) {
+                    // the direct (re-walk) mode reads the text from global memory: no staged bytes
+                    const bool fin = have && (direct ? step<ROW16, true>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr)
+                                                     : step<ROW16, DEEP>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr));
+                    if (fin) {
                         qst[qi] = t;
                         have = false;
                     }
                 }
+            };
+            {
+                uint32_t nc = 0;
+                for (uint32_t r0 = 0; r0 < nw; r0 += 32) {
+                    if (nc > CCAP - 32) {
+                        __syncwarp();
+                        run_cont(nc);
+                        nc = 0;
+                        __syncwarp();
+                    }
+                    const uint32_t i = r0 + lane;
+                    bool cont = false;
+                    uint32_t st = 0, pos = 0;
+                    if (i < nw) {
+                        const uint32_t val = qst[i];
+                        st = val & GLOP_STATE_MASK;
+                        uint32_t t = (val & GLOP_TERM) ? st : 0u;
+                        pos = qoff[i] + g;
+                        const uint32_t endw = BATCH ? qend[i] : endsub;
+                        const bool fin = direct ? step<ROW16, true>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr)
+                                                : step<ROW16, DEEP>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr);
+                        qst[i] = t;
+                        cont = !fin;
+                    }
+                    const uint32_t bm = __ballot_sync(FULL, cont);
+                    if (cont) {
+                        const uint32_t k = nc + __popc(bm & lt);
+                        cst[k] = st;
+                        cpos[k] = pos;
+                        cidx[k] = (uint8_t)i;
+                    }
+                    nc += __popc(bm);
+                }
+                __syncwarp();
+                if (nc) run_cont(nc);
             }
             __syncwarp();
             // (4) records or direct output, in offset order
@@ -929,13 +1011,13 @@ DevProps props_of(int dev) {
     return cache[dev];
 }
 
-template <int FILT, bool BATCH, bool ROW16>
+template <int FILT, bool BATCH, bool ROW16, bool DEEP>
 int launch_t(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st) {
     static std::mutex mu;
     static uint32_t set_for[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
-    auto fn = scan_kernel<FILT, BATCH, ROW16>;
+    auto fn = scan_kernel<FILT, BATCH, ROW16, DEEP>;
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev >= 0 && dev < 64 && set_for[dev] < smem) {
@@ -1038,7 +1120,7 @@ int launch_scan(const ScanLaunch &L) {
     if (A.gram_len) off += (1u << A.bm_log2) / 8;
     off = align_up(off, 128);
     kp.off_grams = off;
-    const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * 16u : 0u;
+    const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * (A.gram_len == 4 ? 8u : 16u) : 0u;
     const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + NSTAGE * kp.slot_bytes + 32 * QBYTES;
     kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
     if (kp.grams_in_smem) off += gram_bytes;
@@ -1066,15 +1148,20 @@ int launch_scan(const ScanLaunch &L) {
     kp.rec_slots = W.rec_slots;
 
     const bool r16 = A.row16 != 0;
-#define GLOP_LAUNCH(F)                                                                                   \
-    return batch ? (r16 ? launch_t<F, true, true>(kp, smem, grid, L.stream)                              \
-                        : launch_t<F, true, false>(kp, smem, grid, L.stream))                            \
-                 : (r16 ? launch_t<F, false, true>(kp, smem, grid, L.stream)                             \
-                        : launch_t<F, false, false>(kp, smem, grid, L.stream))
-    if (A.gram_len == 0) GLOP_LAUNCH(0);
-    if (A.gram_len == 4) GLOP_LAUNCH(4);
+    const bool deep = A.max_len > 1 && A.max_len - 1 > halo;
+#define GLOP_LAUNCH4(F, D)                                                                               \
+    return batch ? (r16 ? launch_t<F, true, true, D>(kp, smem, grid, L.stream)                           \
+                        : launch_t<F, true, false, D>(kp, smem, grid, L.stream))                         \
+                 : (r16 ? launch_t<F, false, true, D>(kp, smem, grid, L.stream)                          \
+                        : launch_t<F, false, false, D>(kp, smem, grid, L.stream))
+#define GLOP_LAUNCH(F)              \
+    if (deep) GLOP_LAUNCH4(F, true); \
+    GLOP_LAUNCH4(F, false)
+    if (A.gram_len == 0) { GLOP_LAUNCH(0); }
+    if (A.gram_len == 4) { GLOP_LAUNCH(4); }
     GLOP_LAUNCH(8);
 #undef GLOP_LAUNCH
+#undef GLOP_LAUNCH4
 }
 
 }  // namespace glop
