@@ -49,7 +49,7 @@ namespace {
 constexpr uint32_t SUB = kSubTile;
 constexpr uint32_t NCONS = kConsumers;
 constexpr uint32_t CHUNK = kChunk;
-constexpr uint32_t NSTAGE = 3;
+constexpr uint32_t NSTAGE = 3;  // ring slots at most (a launch uses p.nstage = 2 or 3)
 constexpr uint32_t THREADS = 32 * (NCONS + 1);
 constexpr uint32_t SEGW = 32;  // segment boundaries kept on chip per sub-tile
 constexpr uint32_t HALO_CAP = 1024;
@@ -95,7 +95,7 @@ struct KParams {
     uint32_t rec_cap_cta;  // record slots per block
     uint64_t rec_slots;    // record slots in the workspace
     uint64_t n_sub, n_chunks;
-    uint32_t halo, slot_bytes, hot_n, grams_in_smem, aligned;
+    uint32_t halo, slot_bytes, hot_n, grams_in_smem, aligned, nstage;
     uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring, off_q;
     long long spin_budget;
     uint32_t barrier_extra;  // fault injection for tests: grid barriers wait for this many absent blocks
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         uint4 *rdst = reinterpret_cast<uint4 *>(smem + p.off_rows);
         for (uint32_t i = tid; i < n16; i += THREADS) rdst[i] = __ldg(rsrc + i);
         if (tid == 0) {
-            for (uint32_t s = 0; s < NSTAGE; ++s) {
+            for (uint32_t s = 0; s < p.nstage; ++s) {
                 mbar_init(&mc->full[s], 1);
                 mbar_init(&mc->empty[s], NCONS);
             }
@@ -810,10 +810,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     if (warp == 0) {
         // producer: chunk tickets -> ring slots
         for (uint32_t cs = 0;; ++cs) {
-            const uint32_t slot = cs % NSTAGE;
-            if (cs >= NSTAGE) {
+            const uint32_t slot = cs % p.nstage;
+            if (cs >= p.nstage) {
                 uint32_t ok = 1;
-                if (lane == 0) ok = mbar_wait(&mc->empty[slot], ((cs / NSTAGE) - 1) & 1u, p.spin_budget) ? 1u : 0u;
+                if (lane == 0) ok = mbar_wait(&mc->empty[slot], ((cs / p.nstage) - 1) & 1u, p.spin_budget) ? 1u : 0u;
                 ok = __shfl_sync(FULL, ok, 0);
                 if (!ok) {
                     if (lane == 0) atomicOr(p.hdr, WS_TIMEOUT);
@@ -854,8 +854,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     } else {
         const uint32_t cw = warp - 1;
         for (uint32_t cs = 0;; ++cs) {
-            const uint32_t slot = cs % NSTAGE;
-            if (!mbar_wait(&mc->full[slot], (cs / NSTAGE) & 1u, p.spin_budget)) {
+            const uint32_t slot = cs % p.nstage;
+            if (!mbar_wait(&mc->full[slot], (cs / p.nstage) & 1u, p.spin_budget)) {
                 if (lane == 0) atomicOr(p.hdr, WS_TIMEOUT);
                 break;
             }
@@ -952,28 +952,40 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             e += v[q];
         }
         __syncthreads();
+        // Software pipeline over this warp's sub-tiles x, x + 32, ...: the
+        // descriptor two sub-tiles ahead and the first 32 records one
+        // sub-tile ahead load while the current sub-tile expands.
+        auto load_desc = [&](uint32_t x) -> uint4 {
+            uint4 d = make_uint4(0, 0, 0, 0);
+            if (x < np) GLOP_CK(p.hdr, p0 + x < p.n_sub, 32, p0 + x) d = __ldcg(reinterpret_cast<const uint4 *>(p.desc + p0 + x));
+            return d;
+        };
+        // record r of a sub-tile (0s past its end): (f0, f1, lo, c)
+        auto load_rec = [&](const uint4 &d, uint32_t r) -> uint4 {
+            uint4 x = make_uint4(0, 0, 0, 0);
+            if (d.y != REC_OVERFLOW && (uint64_t)d.x + d.y <= p.rec_slots && r < d.y) {
+                const uint32_t *rp = p.records + ((size_t)d.x + r) * REC_W;
+                if (BATCH) x = __ldcg(reinterpret_cast<const uint4 *>(rp));
+                else x = make_uint4(__ldcg(rp), 0u, __ldcg(rp + 1), __ldcg(rp + 2));
+            }
+            return x;
+        };
+        uint4 d1 = load_desc(warp), d2 = load_desc(warp + 32);
+        uint4 r1 = load_rec(d1, lane);
         for (uint32_t x = warp; x < np; x += 32) {
             const uint64_t j = p0 + x;
-            uint4 dr = make_uint4(0, 0, 0, 0);
-            GLOP_CK(p.hdr, j < p.n_sub, 32, j) dr = __ldcg(reinterpret_cast<const uint4 *>(p.desc + j));
+            const uint4 dr = d1, rc = r1;
+            d1 = d2;
+            d2 = load_desc(x + 64);
+            r1 = load_rec(d1, lane);
             unsigned long long o = bases[x];
             if (dr.y != REC_OVERFLOW && (uint64_t)dr.x + dr.y > p.rec_slots) {
                 fail_check(p.hdr, 4, dr.x);
             } else if (dr.y != REC_OVERFLOW) {
-                const uint32_t *recs = p.records + (size_t)dr.x * REC_W;
-                for (uint32_t r0 = 0; r0 < dr.y; r0 += 32) {
-                    const uint32_t r = r0 + lane;
-                    uint32_t f0 = 0, f1 = 0, lo = 0, c = 0;
-                    if (r < dr.y) {
-                        const uint32_t *rp = recs + (size_t)r * REC_W;
-                        if (BATCH) {
-                            const uint4 x = __ldcg(reinterpret_cast<const uint4 *>(rp));
-                            f0 = x.x; f1 = x.y; lo = x.z; c = x.w;
-                        } else {
-                            f0 = __ldcg(rp); lo = __ldcg(rp + 1); c = __ldcg(rp + 2);
-                        }
-                    }
-                    o += expand(lo, c, f0, f1, o);
+                o += expand(rc.z, rc.w, rc.x, rc.y, o);
+                for (uint32_t r0 = 32; r0 < dr.y; r0 += 32) {
+                    const uint4 rr = load_rec(dr, r0 + lane);
+                    o += expand(rr.z, rr.w, rr.x, rr.y, o);
                 }
             } else {
                 // the records did not fit: walk the sub-tile again from global memory
@@ -1113,35 +1125,45 @@ int launch_scan(const ScanLaunch &L) {
     if (const char *e = std::getenv("GLOP_TEST_BARRIER_EXTRA")) kp.barrier_extra = (uint32_t)std::strtoul(e, nullptr, 10);
     if (const char *e = std::getenv("GLOP_TEST_SPIN_BUDGET")) kp.spin_budget = std::strtoll(e, nullptr, 10);
 
-    // shared memory: class map, bitmap, gram table, block state, ring, hot rows
+    // shared memory: class map, bitmap, gram table, block state, ring, hot rows.
+    // The ring has 3 slots, or 2 when that is what lets every walked dense row stay on chip.
     const uint32_t budget = (uint32_t)pr.smem_optin;
-    uint32_t off = 384;
-    kp.off_bitmap = off;
-    if (A.gram_len) off += (1u << A.bm_log2) / 8;
-    off = align_up(off, 128);
-    kp.off_grams = off;
-    const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * (A.gram_len == 4 ? 8u : 16u) : 0u;
-    const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + NSTAGE * kp.slot_bytes + 32 * QBYTES;
-    kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
-    if (kp.grams_in_smem) off += gram_bytes;
-    off = align_up(off, 128);
-    kp.off_misc = off;
-    off += align_up((uint32_t)sizeof(CtaMisc), 128);
-    kp.off_ring = off;
-    off += NSTAGE * kp.slot_bytes;
-    kp.off_q = off;
-    off += 32 * QBYTES;
-    off = align_up(off, 128);
-    kp.off_rows = off;
     const uint32_t row_bytes = A.n_classes * (A.row16 ? 2u : 4u);
-    uint32_t avail = budget > off + 32 ? budget - off - 32 : 0;
-    if (L.smem_budget) avail = std::min(avail, L.smem_budget);
     const uint32_t hot_avail = A.n_dense > A.hot_lo ? A.n_dense - A.hot_lo : 0;
-    kp.hot_n = std::min<uint32_t>(hot_avail, row_bytes ? avail / row_bytes : 0);
-    off += align_up(kp.hot_n * row_bytes + 16, 16);
-    const uint32_t smem = off;
+    auto carve = [&](uint32_t nstage) -> uint32_t {
+        kp.nstage = nstage;
+        uint32_t off = 384;
+        kp.off_bitmap = off;
+        if (A.gram_len) off += (1u << A.bm_log2) / 8;
+        off = align_up(off, 128);
+        kp.off_grams = off;
+        const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * (A.gram_len == 4 ? 8u : 16u) : 0u;
+        const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + nstage * kp.slot_bytes + 32 * QBYTES;
+        kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
+        if (kp.grams_in_smem) off += gram_bytes;
+        off = align_up(off, 128);
+        kp.off_misc = off;
+        off += align_up((uint32_t)sizeof(CtaMisc), 128);
+        kp.off_ring = off;
+        off += nstage * kp.slot_bytes;
+        kp.off_q = off;
+        off += 32 * QBYTES;
+        off = align_up(off, 128);
+        kp.off_rows = off;
+        uint32_t avail = budget > off + 32 ? budget - off - 32 : 0;
+        if (L.smem_budget) avail = std::min(avail, L.smem_budget);
+        kp.hot_n = std::min<uint32_t>(hot_avail, row_bytes ? avail / row_bytes : 0);
+        off += align_up(kp.hot_n * row_bytes + 16, 16);
+        return off;
+    };
+    uint32_t smem = carve(NSTAGE);
+    if (kp.hot_n < hot_avail && !L.smem_budget) {
+        const uint32_t smem2 = carve(2);
+        if (kp.hot_n < hot_avail) smem = carve(NSTAGE);
+        else smem = smem2;
+    }
     if (smem > budget) return 7;
-    if (PB * 8 > NSTAGE * kp.slot_bytes) return 7;
+    if (PB * 8 > kp.nstage * kp.slot_bytes) return 7;
     uint32_t grid = (uint32_t)std::min<uint64_t>(n_chunks, (uint64_t)std::min(pr.sms, (int)kMaxGrid));
     if (grid == 0) grid = 1;
     kp.rec_cap_cta = (uint32_t)std::min<uint64_t>(W.rec_slots / grid, 0xFFFFFFF0ull / grid);
