@@ -970,13 +970,18 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             }
             return x;
         };
-        uint4 d1 = load_desc(warp), d2 = load_desc(warp + 32);
+        // (batch mode, with its wider records, keeps the descriptor one sub-tile ahead only: registers)
+        uint4 d1 = load_desc(warp), d2 = BATCH ? make_uint4(0, 0, 0, 0) : load_desc(warp + 32);
         uint4 r1 = load_rec(d1, lane);
         for (uint32_t x = warp; x < np; x += 32) {
             const uint64_t j = p0 + x;
             const uint4 dr = d1, rc = r1;
-            d1 = d2;
-            d2 = load_desc(x + 64);
+            if (BATCH) {
+                d1 = load_desc(x + 32);
+            } else {
+                d1 = d2;
+                d2 = load_desc(x + 64);
+            }
             r1 = load_rec(d1, lane);
             unsigned long long o = bases[x];
             if (dr.y != REC_OVERFLOW && (uint64_t)dr.x + dr.y > p.rec_slots) {
