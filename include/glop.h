@@ -253,6 +253,25 @@ glop_status glop_plan_destroy(glop_plan plan);
 glop_status glop_scan_noalloc(glop_handle h, const uint8_t *d_text, uint64_t len, glop_match *d_matches,
                               uint64_t capacity, uint64_t *d_count, glop_stream_t stream);
 
+/*
+ * glop_batch_split -- a batch scan's matches as (offset, pattern_id) pairs
+ * plus the run of each segment.  The paper has no counterpart: it serves a
+ * server that batches one request per segment and returns each request its
+ * own matches (8 bytes a match over the host link instead of 12).
+ *
+ * d_matches: the glop_scan_batch output (capacity entries, sorted by
+ * segment); d_count: its device match count (only min(*d_count, capacity)
+ * entries are read).  Writes d_pairs[i] = (offset, pattern_id) of match i
+ * (capacity entries of room) and d_seg_first[s] = the index of the first
+ * match of segment s, for s = 0 .. n_segments (d_seg_first[n_segments] =
+ * the number of matches read), so segment s owns pairs
+ * [d_seg_first[s], d_seg_first[s + 1]).  All pointers are device pointers
+ * owned by the caller; d_pairs must not overlap d_matches.  Queued on stream
+ * after the scan; GLOP_EINVAL for a NULL pointer or n_segments = UINT32_MAX.
+ */
+glop_status glop_batch_split(const glop_batch_match *d_matches, const uint64_t *d_count, uint64_t capacity,
+                             uint32_t n_segments, glop_match *d_pairs, uint64_t *d_seg_first, glop_stream_t stream);
+
 /* glop_destroy -- free the automaton's device memory.  No scan using h may
  * still be in flight.  NULL is accepted. */
 glop_status glop_destroy(glop_handle h);

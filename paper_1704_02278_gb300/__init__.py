@@ -36,7 +36,7 @@ OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_workspace_size", "glop_scan",
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
            "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc", "glop_plan_create",
-           "glop_plan_launch", "glop_plan_destroy", "glop_tune"]
+           "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split"]
 
 
 class GlopError(RuntimeError):
@@ -107,6 +107,8 @@ def lib():
                                 ctypes.POINTER(u32), ctypes.POINTER(glop_compile_opts), vp]
         L.glop_scan_noalloc.restype = ctypes.c_int
         L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
+        L.glop_batch_split.restype = ctypes.c_int
+        L.glop_batch_split.argtypes = [vp, vp, u64, ctypes.c_uint32, vp, vp, vp]
         L.glop_destroy.restype = ctypes.c_int
         L.glop_destroy.argtypes = [vp]
         L.glop_status_str.restype = ctypes.c_char_p
@@ -306,6 +308,18 @@ class Automaton:
             self.close()
         except Exception:
             pass
+
+
+def batch_split(matches, count, n_segments: int, pairs, seg_first, stream=None) -> None:
+    """Queue glop_batch_split: ``matches`` ((cap, 3) int32 CUDA tensor from a batch scan), ``count`` (its
+    int64 count) -> ``pairs`` ((cap, 2) int32) and ``seg_first`` (int64, n_segments + 1).  Asynchronous."""
+    torch = _torch()
+    st = stream if stream is not None else torch.cuda.current_stream(matches.device)
+    cap = matches.shape[0]
+    if pairs.shape[0] < cap or seg_first.numel() < n_segments + 1:
+        raise GlopError(EINVAL, "batch_split: output too small")
+    _check(lib().glop_batch_split(matches.data_ptr(), count.data_ptr(), cap, n_segments, pairs.data_ptr(),
+                                  seg_first.data_ptr(), st.cuda_stream), "glop_batch_split")
 
 
 class Plan:

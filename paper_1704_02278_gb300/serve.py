@@ -88,21 +88,24 @@ class DeviceArena:
 
 
 class _Slot:
-    """Per-stream resources reused by every batch the stream carries (no allocation per batch)."""
+    """Per-stream resources reused by every batch the stream carries (nothing is allocated per batch)."""
 
-    def __init__(self, torch, device, max_requests: int):
+    def __init__(self, torch, device, max_requests: int, out_rows: int):
         self.stream = torch.cuda.Stream(device=device)
         self.seg_host = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
+        self.first_host = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
         self.count_host = torch.empty(1, dtype=torch.int64, pin_memory=True)
-        self.out_host = torch.empty((1 << 16, 3), dtype=torch.int32, pin_memory=True)
-        self.ev_count = torch.cuda.Event()
-        self.ev_done = torch.cuda.Event()
-        self.extra = None  # device output of a rescan
+        self.out_host = torch.empty((out_rows, 2), dtype=torch.int32, pin_memory=True)
+        self.ev = torch.cuda.Event()
+        self.extra = None  # device outputs of a rescan
 
-    def host_out(self, torch, n: int):
+    def host_out(self, torch, n: int, keep: int = 0):
+        """The pinned pair buffer with room for n rows (its first keep rows preserved when it grows)."""
         if self.out_host.shape[0] < n:
-            cap = max(n, 2 * self.out_host.shape[0])
-            self.out_host = torch.empty((cap, 3), dtype=torch.int32, pin_memory=True)
+            old = self.out_host
+            self.out_host = torch.empty((max(n, 2 * old.shape[0]), 2), dtype=torch.int32, pin_memory=True)
+            if keep:
+                self.out_host[:keep].copy_(old[:keep])
         return self.out_host
 
 
@@ -111,119 +114,179 @@ class _Batch:
 
 
 class BatchServer:
-    """Continuous batching of scan requests over resident automata (see module doc)."""
+    """Continuous batching of scan requests over resident automata (see module doc).
+
+    Pending requests wait in one FIFO per pattern set.  A batch takes the set
+    of the oldest pending request and as many of that set's requests, in
+    arrival order, as fit ``max_batch_bytes``, ``max_batch_requests``, the
+    pinned result buffer of a stream slot and the largest free block of the
+    device arena (the group is halved until it fits).  After the scan,
+    ``glop_batch_split`` turns the batch's (segment, offset, pattern_id)
+    matches into (offset, pattern_id) pairs and per-request runs, and only
+    those come back over the host link: the match count and the runs first
+    (with the pairs too when the output bound is small), then exactly the
+    pairs that exist.  The output bound comes from a running estimate of
+    matches per byte of the set (a decaying maximum); a batch that outgrows
+    it is scanned again."""
+
+    EAGER_ROWS = 1 << 16  # output bounds up to this many pairs come back with the count, in one round
 
     def __init__(self, pattern_sets, hbm_budget: int = 8 << 30, max_inflight: int = 4,
                  max_batch_bytes: int = 256 << 20, max_batch_requests: int = 512, keep_matches: bool = False,
-                 device=None):
+                 out_rows: int | None = None, device=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.automata = [Automaton(p) for p in pattern_sets]
         self.arena = DeviceArena(hbm_budget, self.device)
-        self.slots = [_Slot(torch, self.device, max_batch_requests) for _ in range(max_inflight)]
+        if out_rows is None:  # pinned result pairs per stream slot: 1 per 16 bytes of the largest batch
+            out_rows = max(1 << 16, min(max_batch_bytes, hbm_budget) // 16)
+        self.slots = [_Slot(torch, self.device, max_batch_requests, out_rows) for _ in range(max_inflight)]
         self.max_inflight = max_inflight
         self.max_batch_bytes = max_batch_bytes
         self.max_batch_requests = max_batch_requests
+        self.out_rows = out_rows
         self.keep = keep_matches
-        # matches per payload byte per set (running average); a batch whose output outgrows the estimate is
-        # scanned again into a larger output
+        # matches per payload byte per set: a slowly decaying maximum over recent batches (request content
+        # varies, and an output bound that is too small costs a second scan)
         self.density = [0.25] * len(self.automata)
         self.lib = lib()
-        self.stats = {"batches": 0, "rescans": 0, "max_batch_requests": 0, "admission_waits": 0}
+        self.stats = {}
 
     # -- one batch -------------------------------------------------------------
     def _cap(self, si: int, nbytes: int) -> int:
-        return int(self.density[si] * nbytes * 1.5) + 4096
+        return int(self.density[si] * nbytes * 1.25) + 4096
 
-    def _launch(self, reqs, set_index: int, slot: _Slot, cap: int):
+    def _footprint(self, si: int, nbytes: int, nreq: int, cap: int):
+        """(workspace bytes, region sizes..., total) of a batch: text, offsets, count, workspace, the
+        (segment, offset, pattern_id) output, the pairs and the per-request runs."""
+        a = lambda x: (x + 255) // 256 * 256  # noqa: E731
+        ws_bytes = self.automata[si].workspace_bytes(nbytes, nreq)
+        sizes = [a(nbytes), a(8 * (nreq + 1)), 256, a(ws_bytes), a(12 * cap), a(8 * cap), a(8 * (nreq + 1))]
+        return ws_bytes, sizes, sum(sizes)
+
+    def _launch(self, reqs, set_index: int, slot: _Slot, cap: int, fp):
         torch = self.torch
         nbytes = sum(r.payload.numel() for r in reqs)
-        ws_bytes = self.automata[set_index].workspace_bytes(nbytes, len(reqs))
-        t_len = (nbytes + 255) // 256 * 256
-        s_len = (8 * (len(reqs) + 1) + 255) // 256 * 256
-        got = self.arena.alloc(t_len + s_len + 256 + (ws_bytes + 255) // 256 * 256 + 12 * cap)
+        nreq = len(reqs)
+        ws_bytes, sizes, total = fp
+        got = self.arena.alloc(total)
         if got is None:
             return None
         off, ln = got
+        offs = [off]
+        for z in sizes[:-1]:
+            offs.append(offs[-1] + z)
+        t_off, s_off, c_off, w_off, m_off, p_off, f_off = offs
         b = _Batch()
         b.reqs, b.set_index, b.slot, b.region, b.nbytes, b.cap = reqs, set_index, slot, (off, ln), nbytes, cap
-        t_off = off
-        s_off = t_off + t_len
-        c_off = s_off + s_len
-        w_off = c_off + 256
-        m_off = w_off + (ws_bytes + 255) // 256 * 256
+        b.offsets = (t_off, s_off, c_off, w_off, m_off, p_off, f_off, ws_bytes)
         seg = slot.seg_host.numpy()
         seg[0] = 0
-        np.cumsum([r.payload.numel() for r in reqs], out=seg[1:len(reqs) + 1])
-        b.seg = seg[:len(reqs) + 1].copy()
+        np.cumsum([r.payload.numel() for r in reqs], out=seg[1:nreq + 1])
         st = slot.stream
         with torch.cuda.stream(st):
             text = self.arena.view(t_off, nbytes)
-            for r, a0 in zip(reqs, b.seg[:-1]):
-                text[int(a0):int(a0) + r.payload.numel()].copy_(r.payload, non_blocking=True)
-            self.arena.view(s_off, 8 * (len(reqs) + 1)).view(torch.int64).copy_(slot.seg_host[:len(reqs) + 1],
-                                                                                  non_blocking=True)
-        rc = self.lib.glop_scan_batch(self.automata[set_index].handle, self.arena.base + t_off, nbytes,
-                                      self.arena.base + s_off, len(reqs), self.arena.base + m_off, cap,
-                                      self.arena.base + c_off, self.arena.base + w_off, ws_bytes, st.cuda_stream)
-        if rc != OK:
-            self.arena.release(off, ln)
-            raise GlopError(rc, "glop_scan_batch")
+            a0 = 0
+            for r in reqs:
+                n = r.payload.numel()
+                text[a0:a0 + n].copy_(r.payload, non_blocking=True)
+                a0 += n
+            self.arena.view(s_off, 8 * (nreq + 1)).view(torch.int64).copy_(slot.seg_host[:nreq + 1],
+                                                                           non_blocking=True)
+        self._scan_split(b, self.arena.base + m_off, self.arena.base + p_off, cap)
+        b.copied = min(cap, slot.out_host.shape[0]) if cap <= self.EAGER_ROWS else 0
         with torch.cuda.stream(st):
             slot.count_host.copy_(self.arena.view(c_off, 8).view(torch.int64), non_blocking=True)
-        slot.ev_count.record(st)
-        b.offsets = (t_off, s_off, c_off, w_off, m_off, ws_bytes)
+            slot.first_host[:nreq + 1].copy_(self.arena.view(f_off, 8 * (nreq + 1)).view(torch.int64),
+                                             non_blocking=True)
+            if b.copied:
+                slot.out_host[:b.copied].copy_(self._pairs_view(b, b.copied), non_blocking=True)
+        slot.ev.record(st)
         b.stage = 1
         return b
 
-    def _fetch(self, b, total: int):
+    def _scan_split(self, b, out_ptr: int, pairs_ptr: int, cap: int):
+        t_off, s_off, c_off, w_off, m_off, p_off, f_off, ws_bytes = b.offsets
+        base, st = self.arena.base, b.slot.stream.cuda_stream
+        rc = self.lib.glop_scan_batch(self.automata[b.set_index].handle, base + t_off, b.nbytes, base + s_off,
+                                      len(b.reqs), out_ptr, cap, base + c_off, base + w_off, ws_bytes, st)
+        if rc != OK:
+            raise GlopError(rc, "glop_scan_batch")
+        rc = self.lib.glop_batch_split(out_ptr, base + c_off, cap, len(b.reqs), pairs_ptr, base + f_off, st)
+        if rc != OK:
+            raise GlopError(rc, "glop_batch_split")
+
+    def _pairs_view(self, b, n: int, start: int = 0):
+        if b.slot.extra is not None:
+            return b.slot.extra[1][start:n]
+        p_off = b.offsets[5]
+        return self.arena.view(p_off + 8 * start, 8 * (n - start)).view(self.torch.int32).view(-1, 2)
+
+    def _advance(self, b):
+        """Stage 1 done (count and runs on the host): rescan, fetch the remaining pairs, or finish."""
         torch = self.torch
         slot = b.slot
-        t_off, s_off, c_off, w_off, m_off, ws_bytes = b.offsets
+        total = int(slot.count_host.item())
         if total > b.cap:
-            # the output bound was too small: scan this batch again into a larger output
+            # the output bound was too small: scan the batch again into outputs of the true size
             self.stats["rescans"] += 1
-            slot.extra = torch.empty((total, 3), dtype=torch.int32, device=self.device)
-            rc = self.lib.glop_scan_batch(self.automata[b.set_index].handle, self.arena.base + t_off, b.nbytes,
-                                          self.arena.base + s_off, len(b.reqs), slot.extra.data_ptr(), total,
-                                          self.arena.base + c_off, self.arena.base + w_off, ws_bytes,
-                                          slot.stream.cuda_stream)
-            if rc != OK:
-                raise GlopError(rc, "glop_scan_batch")
-            dev_out = slot.extra
-        else:
-            dev_out = self.arena.view(m_off, 12 * total).view(torch.int32).view(total, 3) if total else None
-        host = slot.host_out(torch, max(total, 1))
-        if total:
-            with torch.cuda.stream(slot.stream):
-                host[:total].copy_(dev_out, non_blocking=True)
-        slot.ev_done.record(slot.stream)
+            slot.extra = (torch.empty((total, 3), dtype=torch.int32, device=self.device),
+                          torch.empty((total, 2), dtype=torch.int32, device=self.device))
+            self._scan_split(b, slot.extra[0].data_ptr(), slot.extra[1].data_ptr(), total)
+            b.cap, b.copied = total, 0
+            f_off, nreq = b.offsets[6], len(b.reqs)
+            with torch.cuda.stream(slot.stream):  # the runs of the full output
+                slot.first_host[:nreq + 1].copy_(self.arena.view(f_off, 8 * (nreq + 1)).view(torch.int64),
+                                                 non_blocking=True)
         b.total = total
-        b.stage = 2
+        if total > b.copied:
+            host = slot.host_out(torch, total, keep=b.copied)
+            with torch.cuda.stream(slot.stream):
+                host[b.copied:total].copy_(self._pairs_view(b, total, b.copied), non_blocking=True)
+            slot.ev.record(slot.stream)
+            b.stage = 2
+            return False
+        return True
 
     def _finish(self, b, now: float):
         slot = b.slot
-        m = slot.out_host[:b.total].numpy().view(np.uint32) if b.total else np.zeros((0, 3), np.uint32)
-        bounds = np.searchsorted(m[:, 0], np.arange(len(b.reqs) + 1))
+        pairs = slot.out_host[:b.total].numpy().view(np.uint32)
+        first = slot.first_host[:len(b.reqs) + 1].numpy()
         for k, r in enumerate(b.reqs):
-            lo, hi = bounds[k], bounds[k + 1]
-            r.count = int(hi - lo)
+            lo, hi = int(first[k]), int(first[k + 1])
+            r.count = hi - lo
             if self.keep:
-                r.matches = m[lo:hi, 1:].copy()
+                r.matches = pairs[lo:hi].copy()
             r.done = now
-        self.density[b.set_index] = 0.8 * self.density[b.set_index] + 0.2 * (b.total / max(b.nbytes, 1))
+        self.density[b.set_index] = max(0.97 * self.density[b.set_index], b.total / max(b.nbytes, 1))
         slot.extra = None
         self.arena.release(*b.region)
         self.stats["batches"] += 1
-        self.stats["max_batch_requests"] = max(self.stats["max_batch_requests"], len(b.reqs))
+        self.stats["requests_per_batch_max"] = max(self.stats["requests_per_batch_max"], len(b.reqs))
+
+    def _group(self, fifo, si):
+        """Requests of set si from its FIFO, in arrival order, within the batch limits."""
+        group, nbytes = [], 0
+        for r in fifo:
+            sz = r.payload.numel()
+            if group and (nbytes + sz > self.max_batch_bytes or len(group) >= self.max_batch_requests
+                          or self._cap(si, nbytes + sz) > self.out_rows):
+                break
+            group.append(r)
+            nbytes += sz
+        return group
 
     # -- the loop --------------------------------------------------------------
     def serve(self, requests, realtime: bool = True):
         """Serve ``requests`` (sorted by arrival).  realtime: arrivals follow the trace's clock; else all
-        requests are available at once (saturation).  Returns (wall seconds, stats)."""
+        requests are available at once (saturation).  Returns (wall seconds, stats of this call)."""
+        import collections
         torch = self.torch
-        pending = []
+        self.stats = {"batches": 0, "rescans": 0, "requests_per_batch_max": 0, "admission_waits": 0}
+        fifos = [collections.deque() for _ in self.automata]
+        order = collections.deque()  # arrival order over all sets; requests already batched are skipped
+        batched = set()
         inflight = []
         free_slots = list(self.slots)
         nxt = 0
@@ -233,39 +296,41 @@ class BatchServer:
         while done < n:
             now = time.perf_counter() - t0
             while nxt < n and (not realtime or requests[nxt].arrival <= now):
-                pending.append(requests[nxt])
+                r = requests[nxt]
+                fifos[r.set_index].append(r)
+                order.append(r)
                 nxt += 1
             progressed = False
             # completions
             for b in list(inflight):
-                if b.stage == 1 and b.slot.ev_count.query():
-                    self._fetch(b, int(b.slot.count_host.item()))
-                    progressed = True
-                if b.stage == 2 and b.slot.ev_done.query():
-                    self._finish(b, time.perf_counter() - t0)
-                    inflight.remove(b)
-                    free_slots.append(b.slot)
-                    done += len(b.reqs)
-                    progressed = True
+                if not b.slot.ev.query():
+                    continue
+                progressed = True
+                if b.stage == 1 and not self._advance(b):
+                    continue
+                self._finish(b, time.perf_counter() - t0)
+                inflight.remove(b)
+                free_slots.append(b.slot)
+                done += len(b.reqs)
             # new batches while stream slots and device memory allow
-            while pending and free_slots:
-                si = pending[0].set_index
-                group, nbytes = [], 0
-                for r in pending:
-                    if r.set_index != si:
-                        continue
-                    sz = r.payload.numel()
-                    if group and (nbytes + sz > self.max_batch_bytes or len(group) >= self.max_batch_requests):
+            while free_slots:
+                while order and id(order[0]) in batched:
+                    batched.discard(id(order.popleft()))
+                if not order:
+                    break
+                si = order[0].set_index
+                group = self._group(fifos[si], si)
+                while True:
+                    nb = sum(r.payload.numel() for r in group)
+                    cap = self._cap(si, nb)
+                    fp = self._footprint(si, nb, len(group), cap)
+                    if fp[2] <= self.arena.largest_free or len(group) == 1:
                         break
-                    group.append(r)
-                    nbytes += sz
-                b = self._launch(group, si, free_slots[-1], self._cap(si, nbytes))
-                if b is None and len(group) > 1:
-                    group = group[:1]
-                    b = self._launch(group, si, free_slots[-1], self._cap(si, group[0].payload.numel()))
+                    group = group[:(len(group) + 1) // 2]
+                b = self._launch(group, si, free_slots[-1], cap, fp)
                 if b is None and not inflight:
                     # nothing else holds memory: try a minimal output (a larger one is made if needed)
-                    b = self._launch(group, si, free_slots[-1], 4096)
+                    b = self._launch(group, si, free_slots[-1], 4096, self._footprint(si, nb, len(group), 4096))
                 if b is None:
                     self.stats["admission_waits"] += 1
                     if not inflight:
@@ -273,15 +338,13 @@ class BatchServer:
                                         group[0].payload.numel())
                     break
                 free_slots.pop()
-                if len(group) == len(pending):
-                    pending = []
-                else:
-                    ids = {id(r) for r in group}
-                    pending = [r for r in pending if id(r) not in ids]
+                for _ in group:
+                    fifos[si].popleft()
+                batched.update(id(r) for r in group)
                 inflight.append(b)
                 progressed = True
             if not progressed:
-                if realtime and not inflight and not pending and nxt < n:
+                if realtime and not inflight and not order and nxt < n:
                     time.sleep(max(0.0, min(requests[nxt].arrival - (time.perf_counter() - t0), 0.0005)))
         torch.cuda.synchronize(self.device)
         return time.perf_counter() - t0, dict(self.stats)

@@ -70,3 +70,18 @@ def test_plain_server_matches():
     srv.serve(reqs, realtime=False)
     for r, e in zip(reqs, exp):
         assert np.array_equal(r.matches, e), r.rid
+
+
+def test_results_larger_than_pinned_buffer_and_rescans():
+    sets = W.config5_sets()[:2]
+    reqs = _requests(30)
+    for r in reqs:
+        r.set_index %= 2
+    exp = _solo(sets, reqs)
+    srv = serve.BatchServer(sets, hbm_budget=1 << 30, keep_matches=True, out_rows=1024)
+    srv.density = [1e-6, 1e-6]  # output bounds far too small at first: rescans, then results past the buffer
+    wall, st = srv.serve(reqs, realtime=False)
+    assert st["rescans"] > 0
+    for r, e in zip(reqs, exp):
+        assert r.count == len(e), r.rid
+        assert np.array_equal(r.matches, e), r.rid
