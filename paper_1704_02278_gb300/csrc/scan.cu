@@ -576,6 +576,12 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         return L <= SEGW;
     };
 
+    // Phase B copies the first n_ids_s output-list pattern ids into the ring
+    // (free once phase A is over), after the scan bases; expand reads them
+    // there and the rest from global memory.
+    const uint32_t *ids_s = reinterpret_cast<const uint32_t *>(ring + PB * 8);
+    uint32_t n_ids_s = 0;
+
     // Expand up to 32 matching offsets held one per lane (output list lo..lo+c
     // of the deepest terminal state, fields f0/f1) into output slots o, o+1,
     // ...: all patterns of an offset, offsets in lane order.  Returns the
@@ -590,7 +596,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             const unsigned long long pos = o + slot;
             if (slot < tot && pos < p.cap) {
                 uint32_t pid = 0;
-                GLOP_CK(p.hdr, lo_o + (slot - ex_o) < A.n_cum_ids, 25, lo_o) pid = __ldg(A.cum_ids + lo_o + (slot - ex_o));
+                const uint32_t q = lo_o + (slot - ex_o);
+                GLOP_CK(p.hdr, q < A.n_cum_ids, 25, lo_o) pid = q < n_ids_s ? ids_s[q] : __ldg(A.cum_ids + q);
                 if (BATCH) {
                     uint32_t *ob = reinterpret_cast<uint32_t *>(p.out) + 3 * pos;
                     __stcs(ob, f0_o);
@@ -882,6 +889,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     // ================= phase B =================
     const uint32_t G = gridDim.x;
     grid_sync(p.hdr + 8, G + p.barrier_extra, p.spin_budget, p.hdr);
+    {
+        // the ring is free now: stage the output-list ids that fit after the scan bases
+        // (the __syncthreads of the block sums below orders these stores before any read)
+        n_ids_s = min(A.n_cum_ids, (p.nstage * p.slot_bytes - PB * 8) / 4u);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(ring + PB * 8);
+        for (uint32_t i = tid; i < n_ids_s; i += THREADS) dst[i] = __ldg(A.cum_ids + i);
+    }
     const uint64_t R = (p.n_sub + G - 1) / G;
     const uint64_t ra = min(p.n_sub, (uint64_t)blockIdx.x * R), rb = min(p.n_sub, ra + R);
     {
