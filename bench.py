@@ -291,10 +291,17 @@ def run_serve(args, ws, rank):
         reqs = make()
         wall, st = srv.serve(reqs, realtime=True)
         lat = serve.latency_summary(reqs)
-        reqs2 = make()
-        wall2, st2 = srv.serve(reqs2, realtime=False)
-        out[name] = dict(lat, realtime_wall_s=round(wall, 3), saturated_s=round(wall2, 3),
-                         saturated_gbps=round(8.0 * out["bytes"] / wall2 / 1e9, 3), stats=st2,
+        # saturation: every request available at once; three runs (the host loop is sensitive to the
+        # shared host's load), median reported, best kept beside it
+        walls = []
+        for _ in range(3):
+            reqs2 = make()
+            wall2, st2 = srv.serve(reqs2, realtime=False)
+            walls.append(wall2)
+        wmed = statistics.median(walls)
+        out[name] = dict(lat, realtime_wall_s=round(wall, 3), realtime_stats=st, saturated_s=round(wmed, 3),
+                         saturated_gbps=round(8.0 * out["bytes"] / wmed / 1e9, 3),
+                         saturated_gbps_best=round(8.0 * out["bytes"] / min(walls) / 1e9, 3), stats=st2,
                          matches=int(sum(r.count for r in reqs2)))
     line = {"metric": "served p50/p99 latency (ms) and saturated Gbit/s: continuous batching vs plain",
             "value": out["batched"]["saturated_gbps"], "unit": "Gbit/s", "n_gpus": 1, "steps": 1, "warmup": 1,

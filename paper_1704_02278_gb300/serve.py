@@ -133,7 +133,7 @@ class BatchServer:
 
     def __init__(self, pattern_sets, hbm_budget: int = 8 << 30, max_inflight: int = 4,
                  max_batch_bytes: int = 256 << 20, max_batch_requests: int = 512, keep_matches: bool = False,
-                 out_rows: int | None = None, device=None):
+                 out_rows: int | None = None, fast_bytes: int = 1 << 20, device=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -152,6 +152,17 @@ class BatchServer:
         self.density = [0.25] * len(self.automata)
         self.lib = lib()
         self.stats = {}
+        # idle fast path: a lone request of at most fast_bytes while nothing is in flight goes through one
+        # end-to-end glop_scan_host call (copy in, scan, copy back), as a plain loop would
+        self.fast_bytes = fast_bytes
+        self.fast_cap = max(1 << 16, fast_bytes)
+        if fast_bytes:
+            need = ctypes.c_uint64()
+            self.lib.glop_scan_host_staging_size(self.automata[0].handle, fast_bytes, self.fast_cap,
+                                                 ctypes.byref(need))
+            self.fast_staging = torch.empty(int(need.value), dtype=torch.uint8, device=self.device)
+            self.fast_out = torch.empty((self.fast_cap, 2), dtype=torch.int32, pin_memory=True)
+            self.fast_stream = torch.cuda.Stream(device=self.device)
 
     # -- one batch -------------------------------------------------------------
     def _cap(self, si: int, nbytes: int) -> int:
@@ -283,7 +294,8 @@ class BatchServer:
         requests are available at once (saturation).  Returns (wall seconds, stats of this call)."""
         import collections
         torch = self.torch
-        self.stats = {"batches": 0, "rescans": 0, "requests_per_batch_max": 0, "admission_waits": 0}
+        self.stats = {"batches": 0, "rescans": 0, "requests_per_batch_max": 0, "admission_waits": 0, "fast": 0}
+        cnt = ctypes.c_uint64()
         fifos = [collections.deque() for _ in self.automata]
         order = collections.deque()  # arrival order over all sets; requests already batched are skipped
         batched = set()
@@ -318,7 +330,28 @@ class BatchServer:
                     batched.discard(id(order.popleft()))
                 if not order:
                     break
-                si = order[0].set_index
+                r0 = order[0]
+                if (not inflight and len(order) == 1 and self.fast_bytes and
+                        r0.payload.numel() <= self.fast_bytes):
+                    rc = self.lib.glop_scan_host(self.automata[r0.set_index].handle, r0.payload.data_ptr(),
+                                                 r0.payload.numel(), self.fast_out.data_ptr(), self.fast_cap,
+                                                 ctypes.byref(cnt), self.fast_staging.data_ptr(),
+                                                 self.fast_staging.numel(), self.fast_stream.cuda_stream)
+                    if rc == OK:
+                        r0.count = int(cnt.value)
+                        if self.keep:
+                            r0.matches = self.fast_out[:r0.count].numpy().view(np.uint32).copy()
+                        r0.done = time.perf_counter() - t0
+                        fifos[r0.set_index].popleft()
+                        order.popleft()
+                        done += 1
+                        self.stats["fast"] += 1
+                        progressed = True
+                        continue
+                    if rc != EOVERFLOW:
+                        raise GlopError(rc, "glop_scan_host")
+                    # more matches than the fast path holds: scan it as a batch
+                si = r0.set_index
                 group = self._group(fifos[si], si)
                 while True:
                     nb = sum(r.payload.numel() for r in group)
