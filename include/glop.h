@@ -254,6 +254,29 @@ glop_status glop_scan_noalloc(glop_handle h, const uint8_t *d_text, uint64_t len
                               uint64_t capacity, uint64_t *d_count, glop_stream_t stream);
 
 /*
+ * Count-only alert mode: how often each pattern occurs in a buffer, without
+ * the list of locations -- the paper's use case reports the number of
+ * suspect events as well as where they are (Sec. 1); this is the first half
+ * alone, and it writes no match list at all.
+ *
+ * glop_count_workspace_size: device workspace bytes glop_scan_count needs on
+ * this handle (a header plus one counter per automaton state; text_len does
+ * not change it).
+ *
+ * glop_scan_count: d_hist[j] = the number of offsets i with
+ * d_text[i, i + |p_j|) = p_j (n_patterns uint64, device, 8-byte aligned,
+ * overwritten), *d_total = their sum (device uint64) -- the same counts a
+ * glop_scan of d_text would report.  d_workspace is 256-byte aligned and
+ * caller-owned; len at most 2^32 - 1.  Queued on stream; errors as for
+ * glop_scan (GLOP_EINVAL for a NULL or misaligned pointer or a handle of
+ * another device, GLOP_ENOMEM for a small workspace, GLOP_ECUDA); device
+ * conditions (a timeout) through glop_scan_status on d_workspace.
+ */
+glop_status glop_count_workspace_size(glop_handle h, uint64_t text_len, uint64_t *bytes);
+glop_status glop_scan_count(glop_handle h, const uint8_t *d_text, uint64_t len, uint64_t *d_hist, uint64_t *d_total,
+                            void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream);
+
+/*
  * glop_batch_split -- a batch scan's matches as (offset, pattern_id) pairs
  * plus the run of each segment.  The paper has no counterpart: it serves a
  * server that batches one request per segment and returns each request its

@@ -36,7 +36,8 @@ OK, EINVAL, ENOMEM, EOVERFLOW, ECUDA, ETIMEOUT = 0, 1, 2, 3, 4, 5
 SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_workspace_size", "glop_scan",
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
            "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc", "glop_plan_create",
-           "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split"]
+           "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split",
+           "glop_count_workspace_size", "glop_scan_count"]
 
 
 class GlopError(RuntimeError):
@@ -109,6 +110,10 @@ def lib():
         L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
         L.glop_batch_split.restype = ctypes.c_int
         L.glop_batch_split.argtypes = [vp, vp, u64, ctypes.c_uint32, vp, vp, vp]
+        L.glop_count_workspace_size.restype = ctypes.c_int
+        L.glop_count_workspace_size.argtypes = [vp, u64, ctypes.POINTER(u64)]
+        L.glop_scan_count.restype = ctypes.c_int
+        L.glop_scan_count.argtypes = [vp, vp, u64, vp, vp, vp, u64, vp]
         L.glop_destroy.restype = ctypes.c_int
         L.glop_destroy.argtypes = [vp]
         L.glop_status_str.restype = ctypes.c_char_p
@@ -278,6 +283,40 @@ class Automaton:
             if capacity is not None:
                 raise GlopError(EOVERFLOW, "%d matches > capacity %d" % (total, cap))
             cap = total
+
+    def count_workspace(self, device):
+        """A cached device workspace for count_into on this handle."""
+        torch = _torch()
+        need = ctypes.c_uint64()
+        _check(lib().glop_count_workspace_size(self.handle, 0, ctypes.byref(need)), "count workspace size")
+        ws = getattr(self, "_count_ws", None)
+        if ws is None or ws.numel() < need.value or ws.device != torch.device(device):
+            ws = torch.empty(max(int(need.value), 256), dtype=torch.uint8, device=device)
+            self._count_ws = ws
+        return ws
+
+    def count_into(self, text, hist, total, workspace=None, stream=None) -> None:
+        """Queue a count-only scan: ``hist`` (int64 CUDA tensor of n_patterns) gets each pattern's number of
+        occurrences in ``text``, ``total`` (int64, one element) their sum.  Asynchronous."""
+        torch = _torch()
+        ws = workspace if workspace is not None else self.count_workspace(text.device)
+        st = stream if stream is not None else torch.cuda.current_stream(text.device)
+        _check(lib().glop_scan_count(self.handle, text.data_ptr(), text.numel(), hist.data_ptr(), total.data_ptr(),
+                                     ws.data_ptr(), ws.numel(), st.cuda_stream), "glop_scan_count")
+
+    def count(self, text, stream=None):
+        """Per-pattern occurrence counts of ``text`` (uint8 CUDA tensor): (int64 tensor of n_patterns, total)."""
+        torch = _torch()
+        n = max(self.info["n_patterns"], 1)
+        hist = torch.empty(n, dtype=torch.int64, device=text.device)
+        total = torch.empty(1, dtype=torch.int64, device=text.device)
+        ws = self.count_workspace(text.device)
+        self.count_into(text, hist, total, workspace=ws, stream=stream)
+        st = lib().glop_scan_status(ws.data_ptr(), (stream or torch.cuda.current_stream(text.device)).cuda_stream,
+                                    None)
+        if st != OK:
+            raise GlopError(st, "glop_scan_count")
+        return hist[:self.info["n_patterns"]], int(total.item())
 
     def scan_host(self, text: np.ndarray, capacity: int, staging=None, stream=None):
         """End-to-end scan of a HOST uint8 array (pinned is fastest): copies in, scans, copies back.

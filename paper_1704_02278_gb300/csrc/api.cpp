@@ -209,6 +209,41 @@ glop_status glop_scan(glop_handle h, const uint8_t *d_text, uint64_t len, glop_m
     return do_scan(h, d_text, len, nullptr, 0, d_matches, capacity, d_count, d_workspace, workspace_bytes, stream);
 }
 
+glop_status glop_count_workspace_size(glop_handle h, uint64_t text_len, uint64_t *bytes) {
+    (void)text_len;
+    if (!h || !bytes) return GLOP_EINVAL;
+    *bytes = glop::count_workspace_bytes(h->dev.n_states);
+    return GLOP_OK;
+}
+
+glop_status glop_scan_count(glop_handle h, const uint8_t *d_text, uint64_t len, uint64_t *d_hist, uint64_t *d_total,
+                            void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream) {
+    if (!h || !d_total || !d_workspace || (len && !d_text) || (h->dev.n_patterns && !d_hist)) return GLOP_EINVAL;
+    if (len > 0xFFFFFFFFull) return GLOP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 255) || (reinterpret_cast<uintptr_t>(d_total) & 7) ||
+        (reinterpret_cast<uintptr_t>(d_hist) & 7))
+        return GLOP_EINVAL;
+    if (workspace_bytes < glop::count_workspace_bytes(h->dev.n_states)) return GLOP_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GLOP_ECUDA;
+    if (dev != h->device) return GLOP_EINVAL;
+    glop::ScanLaunch L;
+    L.A = &h->dev;
+    L.text = d_text;
+    L.len = len;
+    L.seg = nullptr;
+    L.n_seg = 0;
+    L.out = nullptr;
+    L.capacity = 0;
+    L.d_count = d_total;
+    L.ws = d_workspace;
+    L.ws_bytes = workspace_bytes;
+    L.stream = reinterpret_cast<cudaStream_t>(stream);
+    L.smem_budget = h->smem_budget;
+    L.hist = reinterpret_cast<unsigned long long *>(d_hist);
+    return (glop_status)glop::launch_scan(L);
+}
+
 glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
                             uint32_t n_segments, glop_batch_match *d_matches, uint64_t capacity, uint64_t *d_count,
                             void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream) {

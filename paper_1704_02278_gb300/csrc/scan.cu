@@ -58,6 +58,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr unsigned long long END_TICKET = ~0ull;
 constexpr uint32_t REC_OVERFLOW = 0xFFFFFFFFu;
 constexpr uint32_t QCAP = 128;   // survivors per walk batch of one warp
+constexpr uint32_t HCACHE = 1024;  // count-only mode: per-block hit table (state, hits), shared memory
 constexpr uint32_t CCAP = 64;    // walks listed for continuation after their first step
 // per-warp queue: offsets (u16), states (u32), walk bounds (u32); continuation states (u32), positions (u32), indexes (u8)
 constexpr uint32_t QBYTES = QCAP * 10 + CCAP * 9;
@@ -92,11 +93,12 @@ struct KParams {
     unsigned long long *sums;
     const uint32_t *tile_seg;
     uint32_t *records;
+    uint32_t *state_hits;  // count-only mode: matched offsets per terminal state (no records, no phase B)
     uint32_t rec_cap_cta;  // record slots per block
     uint64_t rec_slots;    // record slots in the workspace
     uint64_t n_sub, n_chunks;
     uint32_t halo, slot_bytes, hot_n, grams_in_smem, aligned, nstage;
-    uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring, off_q;
+    uint32_t off_bitmap, off_grams, off_rows, off_misc, off_ring, off_q, off_hc;
     long long spin_budget;
     uint32_t barrier_extra;  // fault injection for tests: grid barriers wait for this many absent blocks
 };
@@ -361,6 +363,22 @@ __global__ void init_kernel(uint32_t *hdr, uint32_t *tile_seg, uint64_t n_sub, c
     }
 }
 
+// Count-only mode, after the scan: every pattern in a state's output list
+// occurs once per hit on the state.  hist and total are zero on entry.
+__global__ void count_lists_kernel(const uint32_t *hits, const uint32_t *cum_off, const uint32_t *cum_ids,
+                                   uint32_t n_states, unsigned long long *hist, unsigned long long *total) {
+    unsigned long long sum = 0;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_states; t += gridDim.x * blockDim.x) {
+        const uint32_t h = hits[t];
+        if (!h) continue;
+        const uint32_t lo = cum_off[t], hi = cum_off[t + 1];
+        for (uint32_t q = lo; q < hi; ++q) atomicAdd(hist + cum_ids[q], (unsigned long long)h);
+        sum += (unsigned long long)h * (hi - lo);
+    }
+    for (int d = 16; d; d >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, d);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(total, sum);
+}
+
 template <int FILT, bool BATCH, bool ROW16, bool DEEP>
 __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -383,6 +401,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     // ---- stage the tables: class map, start filter, gram table, hot rows ----
     {
         if (tid < 64) reinterpret_cast<uint32_t *>(cls_s)[tid] = __ldg(reinterpret_cast<const uint32_t *>(A.cls) + tid);
+        if (p.state_hits)
+            for (uint32_t i = tid; i < 2 * HCACHE; i += THREADS) reinterpret_cast<uint32_t *>(smem + p.off_hc)[i] = 0;
         if (tid < 8) fb_s[tid] = 0;
         if (FILT) {
             const uint4 *src = reinterpret_cast<const uint4 *>(A.bitmap);
@@ -635,7 +655,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         const uint32_t lt = (1u << lane) - 1u;
         uint32_t rbase = 0;
         bool ovf = false;
-        if (!direct) {
+        if (!direct && !p.state_hits) {
             if (lane == 0) rbase = atomicAdd(&mc->rec_cursor, total);
             rbase = __shfl_sync(FULL, rbase, 0);
             ovf = (uint64_t)rbase + total > p.rec_cap_cta;
@@ -783,6 +803,20 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 }
                 if (direct) {
                     o += expand(lo, c, f0, f1, o);
+                } else if (p.state_hits) {
+                    // count-only mode: one hit on the offset's deepest terminal state, counted in the
+                    // block's table when the state has (or gets) its slot there, else in global memory
+                    if (t) {
+                        uint32_t *hk = reinterpret_cast<uint32_t *>(smem + p.off_hc);
+                        const uint32_t slot = (t * 0x9E3779B1u) >> (32 - 10);
+                        uint32_t k = hk[slot];
+                        if (k == 0) {
+                            const uint32_t old = atomicCAS(hk + slot, 0u, t);
+                            k = old ? old : t;
+                        }
+                        if (k == t) atomicAdd(hk + HCACHE + slot, 1u);
+                        else atomicAdd(p.state_hits + t, 1u);
+                    }
                 } else {
                     const uint32_t b = __ballot_sync(FULL, t != 0);
                     if (t) {
@@ -800,7 +834,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             }
             __syncwarp();
         }
-        if (!direct) {
+        if (!direct && !p.state_hits) {
             nmatch = warp_sum64(nmatch);
             if (lane == 0) {
                 SubDesc d;
@@ -884,6 +918,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&mc->empty[slot]);
         }
+    }
+
+    // count-only mode ends here (nothing to place, no grid barrier): flush the block's hit table
+    if (p.state_hits) {
+        __syncthreads();
+        const uint32_t *hk = reinterpret_cast<const uint32_t *>(smem + p.off_hc);
+        for (uint32_t i = tid; i < HCACHE; i += THREADS)
+            if (hk[i]) atomicAdd(p.state_hits + hk[i], hk[HCACHE + i]);
+        return;
     }
 
     // ================= phase B =================
@@ -1087,15 +1130,24 @@ WsLayout layout_of(uint64_t len, bool batch) {
 
 uint64_t workspace_bytes(uint64_t len, bool batch) { return layout_of(len, batch).total; }
 
+uint64_t count_workspace_bytes(uint32_t n_states) { return kHeaderBytes + (4ull * n_states + 255) / 256 * 256; }
+
 int launch_scan(const ScanLaunch &L) {
     const GlopDevAutomaton &A = *L.A;
     const bool batch = L.seg != nullptr;
+    const bool count = L.hist != nullptr;  // count-only mode (single buffer): hits per state, no records
+    if (count && batch) return 1;
     const uint64_t n_sub = (L.len + SUB - 1) / SUB;
     const uint64_t n_chunks = (n_sub + NCONS - 1) / NCONS;
     const WsLayout W = layout_of(L.len, batch);
-    if (L.ws_bytes < W.total) return 2;
+    if (L.ws_bytes < (count ? count_workspace_bytes(A.n_states) : W.total)) return 2;
     uint8_t *ws = reinterpret_cast<uint8_t *>(L.ws);
     uint32_t *hdr = reinterpret_cast<uint32_t *>(ws);
+    uint32_t *hits = count ? reinterpret_cast<uint32_t *>(ws + kHeaderBytes) : nullptr;
+    if (count && (cudaMemsetAsync(L.hist, 0, 8ull * A.n_patterns, L.stream) != cudaSuccess ||
+                  cudaMemsetAsync(L.d_count, 0, 8, L.stream) != cudaSuccess ||
+                  cudaMemsetAsync(hits, 0, 4ull * A.n_states, L.stream) != cudaSuccess))
+        return 4;
     const bool nothing = (A.n_patterns == 0) || n_sub == 0 || (batch && L.n_seg == 0);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 4;
@@ -1126,10 +1178,12 @@ int launch_scan(const ScanLaunch &L) {
     kp.cap = L.capacity;
     kp.d_count = reinterpret_cast<unsigned long long *>(L.d_count);
     kp.hdr = hdr;
-    kp.desc = reinterpret_cast<SubDesc *>(ws + W.desc);
-    kp.sums = reinterpret_cast<unsigned long long *>(ws + W.sums);
-    kp.tile_seg = reinterpret_cast<const uint32_t *>(ws + W.tile_seg);
-    kp.records = reinterpret_cast<uint32_t *>(ws + W.records);
+    // (count-only mode uses none of the descriptors, sums or records: its workspace is the header and hits)
+    kp.desc = count ? nullptr : reinterpret_cast<SubDesc *>(ws + W.desc);
+    kp.sums = count ? nullptr : reinterpret_cast<unsigned long long *>(ws + W.sums);
+    kp.tile_seg = count ? nullptr : reinterpret_cast<const uint32_t *>(ws + W.tile_seg);
+    kp.records = count ? nullptr : reinterpret_cast<uint32_t *>(ws + W.records);
+    kp.state_hits = hits;
     kp.n_sub = n_sub;
     kp.n_chunks = n_chunks;
     uint32_t halo = A.max_len > 1 ? A.max_len - 1 : 0;
@@ -1157,7 +1211,8 @@ int launch_scan(const ScanLaunch &L) {
         off = align_up(off, 128);
         kp.off_grams = off;
         const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * (A.gram_len == 4 ? 8u : 16u) : 0u;
-        const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + nstage * kp.slot_bytes + 32 * QBYTES;
+        const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + nstage * kp.slot_bytes + 32 * QBYTES +
+                                     (count ? 8 * HCACHE : 0);
         kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
         if (kp.grams_in_smem) off += gram_bytes;
         off = align_up(off, 128);
@@ -1168,6 +1223,8 @@ int launch_scan(const ScanLaunch &L) {
         kp.off_q = off;
         off += 32 * QBYTES;
         off = align_up(off, 128);
+        kp.off_hc = off;
+        if (count) off += 8 * HCACHE;
         kp.off_rows = off;
         uint32_t avail = budget > off + 32 ? budget - off - 32 : 0;
         if (L.smem_budget) avail = std::min(avail, L.smem_budget);
@@ -1175,10 +1232,11 @@ int launch_scan(const ScanLaunch &L) {
         off += align_up(kp.hot_n * row_bytes + 16, 16);
         return off;
     };
+    // (3 slots unless 2 let every walked dense row on chip, or 3 do not fit beside the tables at all)
     uint32_t smem = carve(NSTAGE);
-    if (kp.hot_n < hot_avail && !L.smem_budget) {
+    if ((kp.hot_n < hot_avail && !L.smem_budget) || smem > budget) {
         const uint32_t smem2 = carve(2);
-        if (kp.hot_n < hot_avail) smem = carve(NSTAGE);
+        if ((kp.hot_n < hot_avail || smem2 > budget) && smem <= budget) smem = carve(NSTAGE);
         else smem = smem2;
     }
     if (smem > budget) return 7;
@@ -1190,6 +1248,7 @@ int launch_scan(const ScanLaunch &L) {
 
     const bool r16 = A.row16 != 0;
     const bool deep = A.max_len > 1 && A.max_len - 1 > halo;
+    auto dispatch = [&]() -> int {
 #define GLOP_LAUNCH4(F, D)                                                                               \
     return batch ? (r16 ? launch_t<F, true, true, D>(kp, smem, grid, L.stream)                           \
                         : launch_t<F, true, false, D>(kp, smem, grid, L.stream))                         \
@@ -1198,11 +1257,19 @@ int launch_scan(const ScanLaunch &L) {
 #define GLOP_LAUNCH(F)              \
     if (deep) GLOP_LAUNCH4(F, true); \
     GLOP_LAUNCH4(F, false)
-    if (A.gram_len == 0) { GLOP_LAUNCH(0); }
-    if (A.gram_len == 4) { GLOP_LAUNCH(4); }
-    GLOP_LAUNCH(8);
+        if (A.gram_len == 0) { GLOP_LAUNCH(0); }
+        if (A.gram_len == 4) { GLOP_LAUNCH(4); }
+        GLOP_LAUNCH(8);
 #undef GLOP_LAUNCH
 #undef GLOP_LAUNCH4
+    };
+    const int rc = dispatch();
+    if (rc || !count) return rc;
+    // count-only mode: spread each state's hits over its output list
+    const uint32_t cb = (uint32_t)std::min<uint64_t>((A.n_states + 255) / 256, (uint64_t)pr.sms * 8);
+    count_lists_kernel<<<cb ? cb : 1, 256, 0, L.stream>>>(kp.state_hits, A.cum_off, A.cum_ids, A.n_states, L.hist,
+                                                          reinterpret_cast<unsigned long long *>(L.d_count));
+    return cudaGetLastError() == cudaSuccess ? 0 : 4;
 }
 
 }  // namespace glop

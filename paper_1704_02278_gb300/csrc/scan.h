@@ -32,6 +32,7 @@ struct ScanLaunch {
     uint64_t ws_bytes;
     cudaStream_t stream;
     uint32_t smem_budget;  // 0 = library default
+    unsigned long long *hist = nullptr;  // count-only mode: per-pattern counts (n_patterns); d_count = their sum
 };
 
 // Workspace: header, one descriptor per sub-tile, block sums, (batch) the
@@ -39,6 +40,8 @@ struct ScanLaunch {
 // with a match -- room for one record per 8 text bytes.  A sub-tile whose
 // records do not fit is walked a second time instead; results stay exact.
 uint64_t workspace_bytes(uint64_t len, bool batch);
+// Count-only mode: the header, then one uint32 hit counter per automaton state.
+uint64_t count_workspace_bytes(uint32_t n_states);
 // returns a glop_status value
 int launch_scan(const ScanLaunch &L);
 
