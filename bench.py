@@ -255,6 +255,133 @@ def cpu_baseline(w, budget_s: float = 20.0):
                       "Aho-Corasick oracle" % (n >> 20, len(times), 8.0 * n / statistics.median(times) / 1e9)}
 
 
+def run_prefix_fp(args, ws, rank):
+    """False positives of the paper's 8-byte prefix matching (Sec. 5): every pattern cut to its first
+    8 bytes reports a superset of the exact matches; the extra reports are the false positives."""
+    if rank != 0:
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1704_02278_gb300 as glop
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    res = {}
+    for name, w in (("syslog-256MiB-1000pat", W.config2()), ("dpi-2GiB-20000sig", W.config3())):
+        text = torch.from_numpy(w.text).to(dev)
+        seg = None if w.seg is None else torch.from_numpy(w.seg.view(np.int64).copy()).to(dev)
+        row = {}
+        for k in (0, 8):
+            a = glop.Automaton(w.patterns, prefix_len=k)
+            if seg is None:
+                m, n = a.scan(text)
+                run = lambda: a.scan_into(text, m, cnt)  # noqa: E731
+            else:
+                m, n = a.scan_batch(text, seg)
+                run = lambda: a.scan_batch_into(text, seg, m, cnt)  # noqa: E731
+            cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+            for _ in range(3):
+                run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 10
+            row["exact" if k == 0 else "prefix8"] = {"matches": int(n), "ms": round(ms, 4),
+                                                     "gbps": round(8.0 * w.nbytes / ms / 1e6, 1)}
+            del m
+            a.close()
+            torch.cuda.empty_cache()
+        ex, pr = row["exact"]["matches"], row["prefix8"]["matches"]
+        row["false_positives"] = pr - ex
+        row["fp_rate"] = (pr - ex) / pr if pr else 0.0
+        res[name] = row
+        del text
+        torch.cuda.empty_cache()
+    line = {"metric": "false-positive rate of 8-byte prefix matching (false reports / prefix-mode reports)",
+            "value": res["syslog-256MiB-1000pat"]["fp_rate"], "unit": "fraction", "n_gpus": 1, "steps": 10,
+            "warmup": 3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": "prefix8-fp (configs 2 and 3)"}, "prefix_fp": res}
+    print(json.dumps(line), flush=True)
+
+
+def run_stream(args, ws, rank):
+    """Streaming ingestion of config 2 (256 MiB syslog, 1,000 patterns) from pinned host memory in 16 MiB
+    chunks: the two-slot StreamScanner (uploads under scans, halo carried on the device) against the same
+    chunks scanned one after another through glop_scan_host, and against one glop_scan_host call."""
+    if rank != 0:
+        return
+    import ctypes
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1704_02278_gb300 as glop
+    from paper_1704_02278_gb300.stream import StreamScanner
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = W.config2()
+    N = w.nbytes
+    chunk = 16 << 20
+    host = torch.from_numpy(w.text).pin_memory()
+    chunks = [host[i:i + chunk] for i in range(0, N, chunk)]
+    a = glop.Automaton(w.patterns)
+    sc = StreamScanner(a, chunk_bytes=chunk, out_rows=8 << 20)
+
+    def streamed():
+        n = 0
+        for c in chunks:
+            n += len(sc.feed(c))
+        return n + len(sc.flush())
+
+    def fresh():
+        sc.pos = sc.buf_start = sc.k = 0
+        sc.tail_len = 0
+        sc.tail_slot = None
+
+    M = streamed()
+    times = []
+    for _ in range(max(args.steps, 3)):
+        fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        assert streamed() == M
+        times.append(time.perf_counter() - t0)
+    # the same chunks, one glop_scan_host call after another (each copies in, scans and copies back)
+    halo = a.info["max_pattern_len"] - 1
+    need = ctypes.c_uint64()
+    cap = 8 << 20
+    glop.lib().glop_scan_host_staging_size(a.handle, chunk + halo, cap, ctypes.byref(need))
+    staging = torch.empty(int(need.value), dtype=torch.uint8, device=dev)
+    hout = torch.empty((cap, 2), dtype=torch.int32, pin_memory=True)
+    cnt = ctypes.c_uint64()
+    st = torch.cuda.Stream()
+    ser = []
+    for _ in range(max(args.steps, 3)):
+        t0 = time.perf_counter()
+        for i in range(0, N, chunk):
+            lo = max(0, i - halo)
+            rc = glop.lib().glop_scan_host(a.handle, host.data_ptr() + lo, min(N, i + chunk) - lo, hout.data_ptr(),
+                                           cap, ctypes.byref(cnt), staging.data_ptr(), staging.numel(),
+                                           st.cuda_stream)
+            assert rc == 0, rc
+        ser.append(time.perf_counter() - t0)
+    tm, ts = statistics.median(times), statistics.median(ser)
+    line = {"metric": "Gbit/s ingested from a host stream (8*N/t, Eq. 1)", "value": round(8.0 * N / tm / 1e9, 3),
+            "unit": "Gbit/s", "n_gpus": 1, "steps": len(times), "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "stream-256MiB-1000pat", "chunk_bytes": chunk, "matches": int(M)},
+            "stream": {"two_slot_s": round(tm, 4), "serial_glop_scan_host_s": round(ts, 4),
+                       "serial_gbps": round(8.0 * N / ts / 1e9, 3),
+                       "note": "timed from the first chunk fed to the last match in host memory (the owned rows of each "
+                "chunk, pinned, relative to the chunk's base)"}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serve(args, ws, rank):
     """Serving trace (Poisson arrivals, log-normal sizes, 8 resident sets): plain per-request scans vs
     continuous batching, in real time (latency) and saturated (throughput)."""
@@ -333,6 +460,12 @@ def main():
         return
     if args.workload.startswith("serve"):
         run_serve(args, ws, rank)
+        return
+    if args.workload == "prefix8-fp":
+        run_prefix_fp(args, ws, rank)
+        return
+    if args.workload == "stream-256MiB-1000pat":
+        run_stream(args, ws, rank)
         return
 
     import torch
@@ -423,6 +556,29 @@ def main():
     algo_bytes = N + n_chunks * min(max(halo - 1, 16), 1024) + rec * 4 * M + 16 * n_tiles
     avg_launch_ms = statistics.mean(per)
     achieved = algo_bytes / (avg_launch_ms / 1e3) / 1e9
+
+    # count-only alert mode (glop_scan_count) on the same input: per-pattern counts, no match list
+    count_only = None
+    if seg is None:
+        hist = torch.empty(max(w.patterns.n, 1), dtype=torch.int64, device=dev)
+        ctot = torch.empty(1, dtype=torch.int64, device=dev)
+        cws = a.count_workspace(dev)
+        for _ in range(args.warmup):
+            a.count_into(text, hist, ctot, workspace=cws, stream=stream)
+        stream.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        csteps = min(args.steps, 500)
+        c0.record(stream)
+        for _ in range(csteps):
+            a.count_into(text, hist, ctot, workspace=cws, stream=stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / csteps
+        assert int(ctot.item()) == M, "count-only total %d != scan count %d" % (int(ctot.item()), M)
+        count_only = {"value": round(8.0 * N / (cms / 1e3) / 1e9, 3), "unit": "Gbit/s", "ms_per_step": round(cms, 5),
+                      "steps": csteps, "gpu_launches_per_step": 3,
+                      "note": "glop_scan_count: per-pattern occurrence counts, no match list written"}
+        del hist, ctot
 
     # batches: the same work as plain per-segment glop_scan launches on the same stream
     per_segment = None
@@ -528,6 +684,8 @@ def main():
             line["walk"] = ws_stats
     if e2e:
         line["e2e"] = e2e
+    if count_only:
+        line["count_only"] = count_only
     if per_segment:
         line["per_segment_launches"] = per_segment
     if not args.no_cpu_baseline:
