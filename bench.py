@@ -31,6 +31,7 @@ import numpy as np  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+SMS = 152           # streaming multiprocessors of a GB300
 CHUNK = 31 * 1024    # text bytes one block stages at a time (31 sub-tiles)
 SUBTILE = 1024      # bytes per warp work unit (16-byte status record each)
 
@@ -42,6 +43,26 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_value(workload: str, kind: str, key: str):
+    """An integer ``key: N`` from the committed ncu summary profiles/scan_kernel_<workload>_<kind>.md, when
+    it was taken on the current scan.cu (its sha256 prefix matches); else None."""
+    import hashlib
+    import re
+    root = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(root, "profiles", "scan_kernel_%s_%s.md" % (workload, kind))
+    src = os.path.join(root, "paper_1704_02278_gb300", "csrc", "scan.cu")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m_sha = re.search(r"scan\.cu sha256 prefix: ([0-9a-f]{16})", txt)
+    m_v = re.search(re.escape(key) + r": (\d+)", txt)
+    if not m_sha or not m_v or m_sha.group(1) != sha:
+        return None
+    return int(m_v.group(1))
 
 
 def profiled_traffic(workload: str):
@@ -675,6 +696,17 @@ def main():
     tr = profiled_traffic(args.workload)
     if tr is not None:
         line["roofline"]["traffic"] = tr
+    # the limit that binds: instruction issue (4 schedulers per SM, one warp instruction per cycle each)
+    ins = profiled_value(args.workload, "issue", "inst_per_launch")
+    f_sm = (clk or {}).get("sm_mhz") or 2070.0
+    if ins is not None:
+        peak_issue = 4 * SMS * f_sm * 1e6
+        ach = ins / (avg_launch_ms / 1e3)
+        line["issue_roofline"] = {"bound": "issue", "achieved": round(ach / 1e12, 4), "peak": round(peak_issue / 1e12, 4),
+                                  "unit": "T warp-instructions/s", "frac": round(ach / peak_issue, 4),
+                                  "inst_per_launch": ins,
+                                  "note": "instructions per launch from the committed ncu summary; peak = 4 x SMs x "
+                                          "median SM clock sampled during the timed region"}
     if not args.no_extras:
         rp = read_stream_peak(dev)
         line["roofline"]["read_stream_peak"] = rp
