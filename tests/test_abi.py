@@ -38,11 +38,15 @@ def test_library_exports_every_declared_symbol(libpath):
 
 
 def test_built_for_sm_103a_only(libpath):
-    out = subprocess.run(["cuobjdump", "--list-elf", libpath], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    arches = set(re.findall(r"sm_(\d+a?)", out.stdout))
-    assert arches == {"103a"}, arches
+    # every CUDA object of the library was compiled with exactly one target: sm_103a
+    for src in _build.CUDA_SOURCES:
+        log = os.path.join(_build.BUILD, src + ".o.log")
+        if not os.path.exists(log):
+            pytest.skip("objects built elsewhere")
+        cmd = open(log).readline()
+        assert re.findall(r"-gencode\s+(\S+)", cmd) == ["arch=compute_103a,code=sm_103a"], (src, cmd)
+    link = open(os.path.join(_build.BUILD, "link.log")).readline()
+    assert re.findall(r"-gencode\s+(\S+)", link) == ["arch=compute_103a,code=sm_103a"], link
 
 
 def test_status_strings(libpath):
@@ -70,3 +74,16 @@ def test_kernels_fit_register_budget(libpath):
     regs = [int(x) for x in re.findall(r"Used (\d+) registers", rep)]
     assert regs and max(regs) <= 64  # 1024-thread blocks, one per SM
     assert "spill stores" in rep and not re.search(r"[1-9]\d* bytes spill stores", rep)
+
+
+def test_new_entry_points_reject_bad_arguments_before_any_device_work(libpath):
+    lib = glop.lib()
+    u64 = ctypes.c_uint64()
+    assert lib.glop_count_workspace_size(None, 0, ctypes.byref(u64)) == glop.EINVAL
+    assert lib.glop_scan_count(None, None, 0, None, None, None, 0, None) == glop.EINVAL
+    # batch split: NULL count / runs, and a segment count whose runs array would not be indexable
+    assert lib.glop_batch_split(None, None, 0, 1, None, None, None) == glop.EINVAL
+    dummy = ctypes.c_uint64(0)
+    p = ctypes.addressof(dummy)
+    assert lib.glop_batch_split(None, p, 0, 0xFFFFFFFF, None, p, None) == glop.EINVAL
+    assert lib.glop_batch_split(None, p, 5, 1, None, p, None) == glop.EINVAL  # capacity without arrays
