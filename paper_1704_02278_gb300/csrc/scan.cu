@@ -882,8 +882,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 mc->slot_tile[slot] = k;
                 mc->slot_nstage[slot] = n_stage;
                 bool tma_ok = true;
-                GLOP_CK(p.hdr, c0 + bulk <= p.len && bulk <= p.slot_bytes && !(reinterpret_cast<uintptr_t>(p.text + c0) & 15) &&
-                                   !(smem_addr(dst) & 15) && (bulk & 15) == 0, 30, bulk) {}
+                // (a bulk copy is issued only when bulk > 0: misaligned text is copied by the lanes above)
+                GLOP_CK(p.hdr, bulk == 0 || (c0 + bulk <= p.len && bulk <= p.slot_bytes &&
+                                              !(reinterpret_cast<uintptr_t>(p.text + c0) & 15) &&
+                                              !(smem_addr(dst) & 15) && (bulk & 15) == 0), 30, bulk) {}
 #ifdef GLOP_BOUNDS_CHECK
                 tma_ok = c0 + bulk <= p.len && bulk <= p.slot_bytes && !(reinterpret_cast<uintptr_t>(p.text + c0) & 15) &&
                          !(smem_addr(dst) & 15) && (bulk & 15) == 0;
