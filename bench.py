@@ -468,7 +468,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the read-stream peak and walk statistics")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the read-stream peak, walk statistics and count-only timing")
     ap.add_argument("--per-segment-steps", type=int, default=1)
     ap.add_argument("--serve-seconds", type=int, default=60)
     ap.add_argument("--serve-hbm-gib", type=int, default=16)
@@ -580,7 +581,7 @@ def main():
 
     # count-only alert mode (glop_scan_count) on the same input: per-pattern counts, no match list
     count_only = None
-    if seg is None:
+    if seg is None and not args.no_extras:
         hist = torch.empty(max(w.patterns.n, 1), dtype=torch.int64, device=dev)
         ctot = torch.empty(1, dtype=torch.int64, device=dev)
         cws = a.count_workspace(dev)
