@@ -228,9 +228,17 @@ def run_reference(args, ws, rank):
         return
     import oracle
     w = make_workload(args.workload)
-    sample = w.text[: min(w.nbytes, args.ref_sample_mib * (1 << 20))]
     cores = os.cpu_count() or 1
     pats = w.patterns.csr()
+    # each step is a bounded sample, sized from a 4 MiB calibration run so that warm-up and timed steps
+    # together take about two minutes (at most --ref-sample-mib MiB per step)
+    cal = w.text[: min(w.nbytes, 4 << 20)]
+    t0 = time.perf_counter()
+    oracle.ac_mt(cal, pats, threads=cores)
+    rate = cal.size / max(time.perf_counter() - t0, 1e-6)
+    per_step = 120.0 / max(args.steps + args.warmup, 1)
+    nbytes = int(min(args.ref_sample_mib << 20, max(256 << 10, rate * per_step)))
+    sample = w.text[: min(w.nbytes, nbytes)]
     for _ in range(args.warmup):
         oracle.ac_mt(sample, pats, threads=cores)
     times = []
@@ -247,8 +255,8 @@ def run_reference(args, ws, rank):
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "sample_bytes": int(sample.size)},
         "cpu_baseline": {"value": round(gbps, 4), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
-                         "sample": "first %d MiB of the workload, multi-threaded Aho-Corasick oracle, %d steps"
-                                   % (sample.size >> 20, args.steps)},
+                         "sample": "first %.2f MiB of the workload per step (sized so all %d steps take about "
+                                   "two minutes), multi-threaded Aho-Corasick oracle" % (sample.size / 2**20, args.steps)},
         "e2e": {"value": round(gbps, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
