@@ -272,17 +272,131 @@ glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint
     return GLOP_OK;
 }
 
+// staging: text | matches | count area (the count, or per piece counts and output bases) | workspace
+constexpr uint64_t kCountArea = 512;
+
 glop_status glop_scan_host_staging_size(glop_handle h, uint64_t len, uint64_t capacity, uint64_t *bytes) {
     if (!h || !bytes) return GLOP_EINVAL;
-    *bytes = al(len) + al(capacity * sizeof(glop_match)) + 256 + glop::workspace_bytes(len, false);
+    *bytes = al(len) + al(capacity * sizeof(glop_match)) + kCountArea + glop::workspace_bytes(len, false);
     return GLOP_OK;
 }
+
+namespace {
+
+// glop_scan_host on long texts: pieces of at least kPieceMin bytes, uploaded on one stream, scanned in order
+// on the caller's stream (each scan places its matches after the previous piece's, from a device word, and
+// covers the next longest-pattern - 1 bytes as look-ahead), and copied back on a third stream as soon as each
+// piece's count is known -- uploads, scans and copy-backs of different pieces overlap.
+constexpr uint64_t kPieceMin = 32ull << 20;
+constexpr uint32_t kMaxPieces = 8;
+
+static_assert((2 * kMaxPieces + 1) * 8 <= 512, "per-piece counts and bases fit the count area");
+
+struct HostPipe {
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t uploaded[kMaxPieces] = {}, scanned[kMaxPieces] = {};
+    uint64_t *pinned = nullptr;  // per piece: match count, header flags
+    bool ok = false;
+};
+
+// Streams, events and pinned words of this host thread on device dev (created once, kept for the process).
+HostPipe *host_pipe(int dev) {
+    thread_local HostPipe pipes[64];
+    if (dev < 0 || dev >= 64) return nullptr;
+    HostPipe &hp = pipes[dev];
+    if (hp.ok) return &hp;
+    if (cudaStreamCreateWithFlags(&hp.up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&hp.pinned, 2 * kMaxPieces * sizeof(uint64_t)) != cudaSuccess)
+        return nullptr;
+    for (uint32_t k = 0; k < kMaxPieces; ++k)
+        if (cudaEventCreateWithFlags(&hp.uploaded[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&hp.scanned[k], cudaEventDisableTiming) != cudaSuccess)
+            return nullptr;
+    hp.ok = true;
+    return &hp;
+}
+
+glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len, glop_match *h_matches,
+                             uint64_t capacity, uint64_t *h_count, uint8_t *d_text, glop_match *d_m, uint64_t *d_c,
+                             void *ws, uint64_t ws_bytes, cudaStream_t st) {
+    HostPipe *hp = host_pipe(h->device);
+    if (!hp) return GLOP_ECUDA;
+    const uint32_t P = (uint32_t)std::min<uint64_t>(kMaxPieces, len / kPieceMin);
+    const uint64_t ps = ((len + P - 1) / P + 1023) / 1024 * 1024;
+    const uint64_t halo = h->dev.max_len ? h->dev.max_len - 1 : 0;
+    uint64_t *d_counts = d_c, *d_bases = d_c + kMaxPieces;  // count area: P counts, P + 1 bases
+    auto lo = [&](uint32_t k) { return std::min<uint64_t>(len, k * ps); };
+    if (cudaMemsetAsync(d_bases, 0, 8, st) != cudaSuccess) return GLOP_ECUDA;
+    for (uint32_t k = 0; k < P; ++k) {
+        const uint64_t a = lo(k), b = lo(k + 1);
+        if (b > a && cudaMemcpyAsync(d_text + a, h_text + a, b - a, cudaMemcpyHostToDevice, hp->up) != cudaSuccess)
+            return GLOP_ECUDA;
+        if (cudaEventRecord(hp->uploaded[k], hp->up) != cudaSuccess) return GLOP_ECUDA;
+    }
+    for (uint32_t k = 0; k < P; ++k) {
+        const uint64_t a = lo(k), b = lo(k + 1), e = std::min(len, b + halo);
+        for (uint32_t q = k; q < P && lo(q) < std::max(e, b); ++q)  // this piece and its look-ahead
+            if (cudaStreamWaitEvent(st, hp->uploaded[q], 0) != cudaSuccess) return GLOP_ECUDA;
+        glop::ScanLaunch L;
+        L.A = &h->dev;
+        L.text = d_text + a;
+        L.len = e - a;
+        L.seg = nullptr;
+        L.n_seg = 0;
+        L.out = d_m;
+        L.capacity = capacity;
+        L.d_count = d_counts + k;
+        L.ws = ws;
+        L.ws_bytes = ws_bytes;
+        L.stream = st;
+        L.smem_budget = h->smem_budget;
+        L.own_len = b - a;
+        L.base_off = (uint32_t)a;
+        L.d_obase = reinterpret_cast<const unsigned long long *>(d_bases + k);
+        L.d_next_base = reinterpret_cast<unsigned long long *>(d_bases + k + 1);
+        if (b == a) {  // an empty piece: its base passes on unchanged
+            if (cudaMemcpyAsync(d_bases + k + 1, d_bases + k, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return GLOP_ECUDA;
+            continue;
+        }
+        const int rc = glop::launch_scan(L);
+        if (rc) return (glop_status)rc;
+        if (cudaMemcpyAsync(hp->pinned + 2 * k, d_counts + k, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hp->pinned + 2 * k + 1, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaEventRecord(hp->scanned[k], st) != cudaSuccess)
+            return GLOP_ECUDA;
+    }
+    uint64_t base = 0;
+    uint32_t flags = 0;
+    for (uint32_t k = 0; k < P; ++k) {
+        if (lo(k + 1) == lo(k)) continue;
+        if (cudaEventSynchronize(hp->scanned[k]) != cudaSuccess) return GLOP_ECUDA;
+        const uint64_t c = hp->pinned[2 * k];
+        flags |= (uint32_t)hp->pinned[2 * k + 1];
+        const uint64_t n = base < capacity ? std::min(c, capacity - base) : 0;
+        if (n && (cudaStreamWaitEvent(hp->down, hp->scanned[k], 0) != cudaSuccess ||
+                  cudaMemcpyAsync(h_matches + base, d_m + base, n * sizeof(glop_match), cudaMemcpyDeviceToHost,
+                                  hp->down) != cudaSuccess))
+            return GLOP_ECUDA;
+        base += c;
+    }
+    if (cudaStreamSynchronize(hp->down) != cudaSuccess) return GLOP_ECUDA;
+    *h_count = base;
+    if (flags & glop::WS_INTERNAL) return GLOP_EINTERNAL;
+    if (flags & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
+    if (base > capacity) return GLOP_EOVERFLOW;
+    return GLOP_OK;
+}
+
+}  // namespace
 
 glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, glop_match *h_matches,
                            uint64_t capacity, uint64_t *h_count, void *d_staging, uint64_t staging_bytes,
                            glop_stream_t stream) {
     if (!h || !h_count || !d_staging || (len && !h_text) || (capacity && !h_matches)) return GLOP_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_staging) & 255) return GLOP_EINVAL;
+    if (len > 0xFFFFFFFFull) return GLOP_EINVAL;
     uint64_t need = 0;
     glop_scan_host_staging_size(h, len, capacity, &need);
     if (staging_bytes < need) return GLOP_ENOMEM;
@@ -290,9 +404,14 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
     uint8_t *d_text = p;
     glop_match *d_m = reinterpret_cast<glop_match *>(p + al(len));
     uint64_t *d_c = reinterpret_cast<uint64_t *>(p + al(len) + al(capacity * sizeof(glop_match)));
-    void *ws = p + al(len) + al(capacity * sizeof(glop_match)) + 256;
+    void *ws = p + al(len) + al(capacity * sizeof(glop_match)) + kCountArea;
     uint64_t ws_bytes = glop::workspace_bytes(len, false);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GLOP_ECUDA;
+    if (dev != h->device) return GLOP_EINVAL;
+    if (len >= 2 * kPieceMin && h->dev.n_patterns)
+        return scan_host_pieces(h, h_text, len, h_matches, capacity, h_count, d_text, d_m, d_c, ws, ws_bytes, st);
     if (len && cudaMemcpyAsync(d_text, h_text, len, cudaMemcpyHostToDevice, st) != cudaSuccess) return GLOP_ECUDA;
     glop_status s = glop_scan(h, d_text, len, d_m, capacity, d_c, ws, ws_bytes, stream);
     if (s != GLOP_OK) return s;

@@ -82,7 +82,11 @@ struct CtaMisc {
 struct KParams {
     GlopDevAutomaton A;
     const uint8_t *text;
-    uint64_t len;
+    uint64_t len;          // bytes a walk may read
+    uint64_t own_len;      // match starts are taken in [0, own_len) (<= len; the rest is look-ahead)
+    uint32_t base_off;     // added to every reported offset (single buffer)
+    const unsigned long long *d_obase;  // device word: output index of this scan's first match (or null: 0)
+    unsigned long long *d_next_base;    // device word: receives that index + this scan's match count (or null)
     const uint64_t *seg;
     uint32_t n_seg;
     void *out;
@@ -641,7 +645,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     auto process = [&](uint64_t j, const TextView &v, uint32_t qw, bool direct, unsigned long long obase) {
         const uint64_t s0 = j * SUB;
         const uint64_t avail = p.len - s0;
-        const uint32_t sub_len = (uint32_t)min((uint64_t)SUB, avail);
+        const uint32_t sub_len = (uint32_t)min((uint64_t)SUB, p.own_len - s0);
         const uint32_t endsub = (uint32_t)min(avail, (uint64_t)0xFFFFFFFFu);
         bool onchip = true;
         if (BATCH) onchip = load_segs(qw, j);
@@ -797,7 +801,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                             f0 = si;
                             f1 = (uint32_t)(iabs - sstart);
                         } else {
-                            f0 = (uint32_t)iabs;
+                            f0 = (uint32_t)iabs + p.base_off;
                         }
                     }
                 }
@@ -966,11 +970,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         before = warp_sum64(before);
         all = warp_sum64(all);
         if (lane == 0) {
-            mc->red[0] = before;
+            const unsigned long long obase = p.d_obase ? *p.d_obase : 0ull;
+            mc->red[0] = obase + before;
             if (blockIdx.x == 0) {
                 *p.d_count = all;
                 *reinterpret_cast<unsigned long long *>(p.hdr + 4) = all;
-                if (all > p.cap) atomicOr(p.hdr, WS_OVERFLOW);
+                if (obase + all > p.cap) atomicOr(p.hdr, WS_OVERFLOW);
+                if (p.d_next_base) *p.d_next_base = obase + all;
             }
         }
     }
@@ -1139,7 +1145,9 @@ int launch_scan(const ScanLaunch &L) {
     const bool batch = L.seg != nullptr;
     const bool count = L.hist != nullptr;  // count-only mode (single buffer): hits per state, no records
     if (count && batch) return 1;
-    const uint64_t n_sub = (L.len + SUB - 1) / SUB;
+    const uint64_t own_len = L.own_len ? std::min(L.own_len, L.len) : L.len;
+    if (batch && own_len != L.len) return 1;
+    const uint64_t n_sub = (own_len + SUB - 1) / SUB;
     const uint64_t n_chunks = (n_sub + NCONS - 1) / NCONS;
     const WsLayout W = layout_of(L.len, batch);
     if (L.ws_bytes < (count ? count_workspace_bytes(A.n_states) : W.total)) return 2;
@@ -1168,12 +1176,24 @@ int launch_scan(const ScanLaunch &L) {
                                                    nothing ? 1 : 0);
         if (cudaGetLastError() != cudaSuccess) return 4;
     }
-    if (nothing) return 0;
+    if (nothing) {
+        // a piece with nothing to scan still passes its output base on
+        if (L.d_next_base) {
+            const cudaError_t e = L.d_obase ? cudaMemcpyAsync(L.d_next_base, L.d_obase, 8, cudaMemcpyDeviceToDevice, L.stream)
+                                            : cudaMemsetAsync(L.d_next_base, 0, 8, L.stream);
+            if (e != cudaSuccess) return 4;
+        }
+        return 0;
+    }
 
     KParams kp;
     kp.A = A;
     kp.text = L.text;
     kp.len = L.len;
+    kp.own_len = own_len;
+    kp.base_off = L.base_off;
+    kp.d_obase = L.d_obase;
+    kp.d_next_base = L.d_next_base;
     kp.seg = L.seg;
     kp.n_seg = L.n_seg;
     kp.out = L.out;

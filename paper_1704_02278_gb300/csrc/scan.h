@@ -33,6 +33,13 @@ struct ScanLaunch {
     cudaStream_t stream;
     uint32_t smem_budget;  // 0 = library default
     unsigned long long *hist = nullptr;  // count-only mode: per-pattern counts (n_patterns); d_count = their sum
+    // Pieces of a longer buffer (single buffer only): match starts in [0, own_len) (0 = len; bytes up to
+    // len are look-ahead for walks), reported offsets + base_off, the first match written at output index
+    // *d_obase (null: 0), and *d_next_base = that index + this piece's match count (null: not written).
+    uint64_t own_len = 0;
+    uint32_t base_off = 0;
+    const unsigned long long *d_obase = nullptr;
+    unsigned long long *d_next_base = nullptr;
 };
 
 // Workspace: header, one descriptor per sub-tile, block sums, (batch) the

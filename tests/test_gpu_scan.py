@@ -185,3 +185,31 @@ def test_dense_matches_overflow_scratch():
     exp = oracle.ac_mt(text, pats)
     assert n == len(exp)
     assert np.array_equal(got, exp)
+
+
+def test_scan_host_pieces_cross_boundaries_and_overflow():
+    # long texts are uploaded, scanned and copied back in overlapping pieces; a 199-byte pattern planted
+    # across the piece boundaries must be found once, and an overflow keeps the sorted prefix
+    w = W.config2(100 * W.MiB + 17)
+    longp = bytes(range(1, 200))
+    pats = W.Patterns.from_list(w.patterns.as_list() + [longp])
+    text = w.text.copy()
+    n = text.size
+    pieces = min(8, n // (32 << 20))
+    ps = ((n + pieces - 1) // pieces + 1023) // 1024 * 1024
+    bounds = list(range(ps, n, ps))
+    for b in bounds:  # one copy across each piece boundary
+        text[b - 100:b + 99] = np.frombuffer(longp, np.uint8)
+    exp = oracle.ac_mt(text, pats.csr())
+    a = glop.Automaton(pats)
+    pinned = torch.from_numpy(text).pin_memory().numpy()
+    got, total = a.scan_host(pinned, capacity=len(exp) + 10)
+    assert total == len(exp)
+    assert np.array_equal(got, exp)
+    long_at = got[got[:, 1] == len(pats.as_list()) - 1][:, 0]
+    assert set(b - 100 for b in bounds) <= set(int(x) for x in long_at)
+    cap = len(exp) // 2 + 7
+    got2, total2 = a.scan_host(text, capacity=cap)
+    assert total2 == len(exp)
+    assert np.array_equal(got2, exp[:cap])
+    a.close()
