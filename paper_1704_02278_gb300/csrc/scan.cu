@@ -77,6 +77,7 @@ struct CtaMisc {
     unsigned long long red[32];
     unsigned long long segl[32][SEGW + 1];
     uint32_t seg_a[32], seg_L[32];
+    uint32_t slot_seg[NSTAGE][32];  // batches: first segment of each sub-tile of the slot's chunk (+ the next)
 };
 
 struct KParams {
@@ -578,27 +579,6 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         return iabs < send;
     };
 
-    // the segment list of sub-tile j into warp slot cw (whole warp)
-    auto load_segs = [&](uint32_t cw, uint64_t j) -> bool {
-        if (lane == 0) {
-            uint32_t a = 0, e = 1;
-            GLOP_CK(p.hdr, j + 1 <= p.n_sub, 22, j) {
-                a = __ldg(p.tile_seg + j);
-                e = __ldg(p.tile_seg + j + 1) + 1;
-            }
-            if (e > p.n_seg) e = p.n_seg;
-            mc->seg_a[cw] = a;
-            mc->seg_L[cw] = e - a;
-        }
-        __syncwarp();
-        const uint32_t L = mc->seg_L[cw], a = mc->seg_a[cw];
-        if (L <= SEGW)
-            for (uint32_t x = lane; x <= L; x += 32)
-                GLOP_CK(p.hdr, a + x <= p.n_seg && cw < 32, 23, a + x)
-                mc->segl[cw][x] = __ldg(reinterpret_cast<const unsigned long long *>(p.seg) + a + x);
-        __syncwarp();
-        return L <= SEGW;
-    };
 
     // Phase B copies the first n_ids_s output-list pattern ids into the ring
     // (free once phase A is over), after the scan bases; expand reads them
@@ -642,14 +622,49 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     // ends, (4) in offset order, record mode writes (offset, output list)
     // records to this block's scratch slice and the sub-tile descriptor;
     // direct mode (output position known) expands straight into the output.
-    auto process = [&](uint64_t j, const TextView &v, uint32_t qw, bool direct, unsigned long long obase) {
+    auto process = [&](uint64_t j, const TextView &v, uint32_t qw, bool direct, unsigned long long obase,
+                       const uint32_t *sseg) {
         const uint64_t s0 = j * SUB;
         const uint64_t avail = p.len - s0;
         const uint32_t sub_len = (uint32_t)min((uint64_t)SUB, p.own_len - s0);
         const uint32_t endsub = (uint32_t)min(avail, (uint64_t)0xFFFFFFFFu);
         bool onchip = true;
-        if (BATCH) onchip = load_segs(qw, j);
+        // batches: the segment boundaries of the sub-tile load into registers while the start filter runs
+        uint32_t sa = 0, sL = 0;
+        unsigned long long pb0 = 0, pb1 = 0;
+        if (BATCH) {
+            uint32_t a = 0, e = 1;
+            if (sseg) {
+                a = sseg[0];
+                e = sseg[1] + 1;
+            } else {
+                GLOP_CK(p.hdr, j + 1 <= p.n_sub, 22, j) {
+                    a = __ldg(p.tile_seg + j);
+                    e = __ldg(p.tile_seg + j + 1) + 1;
+                }
+            }
+            if (e > p.n_seg) e = p.n_seg;
+            sa = a;
+            sL = e - a;
+            if (sL <= SEGW) {
+                const unsigned long long *sb = reinterpret_cast<const unsigned long long *>(p.seg) + a;
+                if (lane <= sL) GLOP_CK(p.hdr, a + lane <= p.n_seg, 23, a + lane) pb0 = __ldg(sb + lane);
+                if (lane == 0 && sL == SEGW) GLOP_CK(p.hdr, a + SEGW <= p.n_seg, 23, a + SEGW) pb1 = __ldg(sb + SEGW);
+            }
+        }
         const uint32_t mask = filter(v, sub_len, avail);
+        if (BATCH) {
+            if (lane == 0) {
+                mc->seg_a[qw] = sa;
+                mc->seg_L[qw] = sL;
+            }
+            if (sL <= SEGW) {
+                if (lane <= sL) mc->segl[qw][lane] = pb0;
+                if (lane == 0 && sL == SEGW) mc->segl[qw][SEGW] = pb1;
+            }
+            __syncwarp();
+            onchip = sL <= SEGW;
+        }
         const uint32_t n = __popc(mask);
         const uint32_t incl = warp_incl_scan(n, lane), excl = incl - n, total = __shfl_sync(FULL, incl, 31);
         uint8_t *qbase = smem + p.off_q + qw * QBYTES;
@@ -881,6 +896,9 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             const uint32_t bulk = p.aligned ? (n_stage & ~15u) : 0u;
             for (uint32_t y = bulk + lane; y < n_stage; y += 32)
                 GLOP_CK(p.hdr, c0 + y < p.len && y < p.slot_bytes, 29, y) dst[y] = __ldg(p.text + c0 + y);
+            // batches: the first segment of each of the chunk's sub-tiles (and of the one after), so consumers
+            // start their segment-boundary loads without a round trip
+            if (BATCH) mc->slot_seg[slot][lane] = __ldg(p.tile_seg + min((uint64_t)(k * NCONS + lane), (uint64_t)p.n_sub));
             __syncwarp();
             if (lane == 0) {
                 mc->slot_tile[slot] = k;
@@ -919,7 +937,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 v.avail = p.len - j * SUB;
                 v.hdr = p.hdr;
 #endif
-                process(j, v, cw, false, 0ull);
+                process(j, v, cw, false, 0ull, BATCH ? &mc->slot_seg[slot][cw] : nullptr);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&mc->empty[slot]);
@@ -1067,7 +1085,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 gv.avail = p.len - j * SUB;
                 gv.hdr = p.hdr;
 #endif
-                process(j, gv, warp, true, o);
+                process(j, gv, warp, true, o, nullptr);
             }
         }
         running += ptot;
