@@ -54,7 +54,7 @@ def _bind(lib):
     u8p = ctypes.POINTER(ctypes.c_uint8)
     u64p = ctypes.POINTER(ctypes.c_uint64)
     u32pp = ctypes.POINTER(ctypes.POINTER(ctypes.c_uint32))
-    for name in ("oracle_naive", "oracle_ac"):
+    for name in ("oracle_naive", "oracle_ac", "oracle_kmp"):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [u8p, ctypes.c_uint64, u8p, u64p, ctypes.c_uint32, ctypes.c_uint32, u32pp, u64p]
@@ -165,6 +165,10 @@ class Oracle:
         th = threads or os.cpu_count() or 1
         return self._run("oracle_ac_mt", text, patterns, prefix_len, int(th))
 
+    def kmp(self, text, patterns, prefix_len: int = 0) -> np.ndarray:
+        """Knuth-Morris-Pratt once per pattern (Sec. 2, Sec. 7): (M, 2) uint32 (offset, pattern_id), sorted."""
+        return self._run("oracle_kmp", text, patterns, prefix_len)
+
     def batch(self, text, seg_offsets, patterns, prefix_len: int = 0, method: str = "ac",
               threads: int | None = None) -> np.ndarray:
         """Per-segment definition: (M, 3) uint32 (segment, offset-in-segment, pattern_id), sorted."""
@@ -211,6 +215,10 @@ def default() -> Oracle:
 
 def naive(text, patterns, prefix_len: int = 0) -> np.ndarray:
     return default().naive(text, patterns, prefix_len)
+
+
+def kmp(text, patterns, prefix_len: int = 0) -> np.ndarray:
+    return default().kmp(text, patterns, prefix_len)
 
 
 def ac(text, patterns, prefix_len: int = 0) -> np.ndarray:

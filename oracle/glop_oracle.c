@@ -34,6 +34,9 @@
  *   oracle_ac_trace -- the goto/failure transitions the automaton takes on a
  *                    text, one line per text byte, for the worked example of
  *                    Sec. 4.
+ *   oracle_kmp    -- Knuth-Morris-Pratt, the single-pattern method the paper
+ *                    compares against (Sec. 2, Sec. 7), run once per pattern:
+ *                    a third way to the same set.
  *
  * Return codes: 0 ok, 1 invalid argument (zero-length pattern, text longer
  * than 2^32-1 bytes, null pointer), 2 out of memory.
@@ -165,6 +168,56 @@ int oracle_naive(const uint8_t *text, uint64_t n, const uint8_t *pat, const uint
     free(b.head);
     free(b.next);
     if (rc) { free(v.a); return rc; }
+    *out = v.a;
+    *count = v.n / 2;
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Knuth-Morris-Pratt, once per pattern (Sec. 2, Sec. 7)                */
+/* ------------------------------------------------------------------ */
+static void sort_records(u32vec *v, int w);
+
+/* For pattern p of length m, border[q] is the length of the longest proper
+ * prefix of p[0..q] that is also a suffix of it.  The scan keeps q = the
+ * length of the longest prefix of p that ends at the current text byte; on
+ * a mismatch it falls back along the borders.  q == m is an occurrence
+ * ending here, which then continues from border[m-1]. */
+int oracle_kmp(const uint8_t *text, uint64_t n, const uint8_t *pat, const uint64_t *poff,
+               uint32_t npat, uint32_t prefix_len, uint32_t **out, uint64_t *count) {
+    *out = NULL;
+    *count = 0;
+    if ((!text && n) || !poff || (npat && !pat) || n > 0xFFFFFFFFull) return OR_EINVAL;
+    uint64_t maxlen;
+    int rc = check_patterns(poff, npat, prefix_len, &maxlen);
+    if (rc) return rc;
+    if (npat == 0 || n == 0) return OR_OK;
+    uint64_t *border = (uint64_t *)malloc((size_t)maxlen * sizeof(uint64_t));
+    if (!border) return OR_ENOMEM;
+    u32vec v = {0, 0, 0};
+    for (uint32_t j = 0; j < npat && !rc; ++j) {
+        const uint8_t *p = pat + poff[j];
+        const uint64_t m = eff_len(poff, j, prefix_len);
+        border[0] = 0;
+        for (uint64_t q = 1, k = 0; q < m; ++q) {
+            while (k > 0 && p[q] != p[k]) k = border[k - 1];
+            if (p[q] == p[k]) ++k;
+            border[q] = k;
+        }
+        for (uint64_t i = 0, q = 0; i < n; ++i) {
+            while (q > 0 && text[i] != p[q]) q = border[q - 1];
+            if (text[i] == p[q]) ++q;
+            if (q == m) {
+                const uint32_t rec[2] = {(uint32_t)(i + 1 - m), j};
+                rc = vec_push(&v, rec, 2);
+                if (rc) break;
+                q = ORACLE_MUTANT == 9 ? 0 : border[m - 1];
+            }
+        }
+    }
+    free(border);
+    if (rc) { free(v.a); return rc; }
+    sort_records(&v, 2);
     *out = v.a;
     *count = v.n / 2;
     return OR_OK;

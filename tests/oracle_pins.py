@@ -5,7 +5,8 @@ the oracle disagrees with something other than itself:
 
 * the worked example of Sec. 4 (patterns {HIS, SHE}, text "SHIS"),
 * exhaustive brute force on tiny inputs (Python slicing, written separately),
-* ``bytes.find`` for single-pattern sets (a library routine),
+* ``bytes.find`` for single-pattern sets (a library routine), also against the
+  Knuth-Morris-Pratt oracle on periodic patterns,
 * closed-form counts (nested "a"/"aa"/"aaa"), duplicates, all 256 byte values,
   the end-of-text rule, chunk boundaries of the multi-threaded scan (Sec. 4),
   the empty set, invalid patterns, relabelling, shift invariance, prefix mode
@@ -46,6 +47,8 @@ def check_all_ways(o, text: bytes, pats, prefix_len=0, threads=(1, 3, 7)):
     assert got_n == exp, ("naive", text, pats, prefix_len, got_n, exp)
     got_a = as_list(o.ac(text, pats, prefix_len))
     assert got_a == exp, ("ac", text, pats, prefix_len, got_a, exp)
+    got_k = as_list(o.kmp(text, pats, prefix_len))
+    assert got_k == exp, ("kmp", text, pats, prefix_len, got_k, exp)
     for th in threads:
         got_m = as_list(o.ac_mt(text, pats, prefix_len, threads=th))
         assert got_m == exp, ("ac_mt", th, text, pats, prefix_len, got_m, exp)
@@ -129,6 +132,23 @@ def pin_single_pattern_find(o):
         assert as_list(o.naive(text, [p])) == exp
         assert as_list(o.ac(text, [p])) == exp
         assert as_list(o.ac_mt(text, [p], threads=5)) == exp
+        assert as_list(o.kmp(text, [p])) == exp
+
+
+def pin_periodic_kmp(o):
+    """Periodic patterns, where Knuth-Morris-Pratt falls back along borders and occurrences overlap
+    (Sec. 2, Sec. 7): every way agrees with brute force and with the overlapping bytes.find sequence."""
+    rnd = random.Random(1977)
+    pats = [b"aa", b"aba", b"abab", b"aabaab", b"abaabaab", b"aaab", b"babbab"]
+    for it in range(60):
+        text = bytes(rnd.choice(b"ab") for _ in range(rnd.randint(0, 200)))
+        for p in pats:
+            exp, at = [], text.find(p)
+            while at >= 0:
+                exp.append((at, 0))
+                at = text.find(p, at + 1)
+            assert as_list(o.kmp(text, [p])) == exp, (p, text)
+        check_all_ways(o, text, pats, threads=(2,))
 
 
 def pin_nested(o):
@@ -190,7 +210,8 @@ def pin_empty_and_invalid(o):
     assert len(o.naive(b"abc", [])) == 0
     assert len(o.ac(b"", [b"a"])) == 0
     assert len(o.batch(b"", [0, 0, 0], [b"a"])) == 0
-    for f in (o.naive, o.ac, o.ac_mt):
+    assert len(o.kmp(b"abc", [])) == 0 and len(o.kmp(b"", [b"a"])) == 0
+    for f in (o.naive, o.ac, o.ac_mt, o.kmp):
         try:
             f(b"abc", [b"a", b""])
         except oracle_mod.OracleError as e:
@@ -247,7 +268,8 @@ def pin_segments(o):
 
 
 ALL_PINS = [
-    pin_worked_example, pin_bruteforce_exhaustive, pin_random_small, pin_single_pattern_find, pin_nested,
+    pin_worked_example, pin_bruteforce_exhaustive, pin_random_small, pin_single_pattern_find, pin_periodic_kmp,
+    pin_nested,
     pin_duplicates, pin_all_byte_values, pin_end_of_text, pin_chunk_boundaries, pin_empty_and_invalid,
     pin_relabel, pin_shift, pin_prefix_mode, pin_segments,
 ]
