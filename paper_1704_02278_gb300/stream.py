@@ -67,7 +67,6 @@ class _Slot:
         self.last_len = 0
         self.uploaded = torch.cuda.Event()  # the chunk's bytes are on the device
         self.done = torch.cuda.Event()      # the scan and its match count's copy-back finished
-        self.busy = False
 
 
 class StreamScanner:
@@ -124,7 +123,6 @@ class StreamScanner:
         # first row at or past the owned end (binary search on the strided column, no copy of it)
         col = m[:, 0]
         keep = bisect.bisect_left(range(n), end, key=lambda i: int(col[i]))
-        s.busy = False
         return StreamResult(b0, m[:keep])
 
     def _scan(self, s, nbytes: int):
@@ -165,7 +163,6 @@ class StreamScanner:
         # queue this chunk's scan, then collect the previous scan (the other slot) while it runs
         self._scan(s, h + n)
         out = self._collect(final=False) if self.pending is not None else _EMPTY
-        s.busy = True
         self.pending = (s, b0, b1)
         # next buffer starts where this scan's ownership ends
         nxt = owned_end(b0, b1, self.halo, False)
