@@ -415,16 +415,23 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
     if (len && cudaMemcpyAsync(d_text, h_text, len, cudaMemcpyHostToDevice, st) != cudaSuccess) return GLOP_ECUDA;
     glop_status s = glop_scan(h, d_text, len, d_m, capacity, d_c, ws, ws_bytes, stream);
     if (s != GLOP_OK) return s;
-    if (cudaMemcpyAsync(h_count, d_c, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GLOP_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
-    uint64_t n = *h_count < capacity ? *h_count : capacity;
-    if (n && cudaMemcpyAsync(h_matches, d_m, n * sizeof(glop_match), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    // the count and the status word come back together (the thread's pinned words): one round trip
+    HostPipe *hp = host_pipe(dev);
+    if (!hp) return GLOP_ECUDA;
+    if (cudaMemcpyAsync(hp->pinned, d_c, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(hp->pinned + 1, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
         return GLOP_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
-    uint32_t hdr0 = 0;
-    if (cudaMemcpy(&hdr0, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GLOP_ECUDA;
+    const uint64_t total = hp->pinned[0];
+    const uint32_t hdr0 = (uint32_t)hp->pinned[1];
+    *h_count = total;
+    uint64_t n = total < capacity ? total : capacity;
+    if (n && (cudaMemcpyAsync(h_matches, d_m, n * sizeof(glop_match), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaStreamSynchronize(st) != cudaSuccess))
+        return GLOP_ECUDA;
+    if (hdr0 & glop::WS_INTERNAL) return GLOP_EINTERNAL;
     if (hdr0 & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
-    if (*h_count > capacity) return GLOP_EOVERFLOW;
+    if (total > capacity) return GLOP_EOVERFLOW;
     return GLOP_OK;
 }
 
