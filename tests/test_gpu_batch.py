@@ -102,3 +102,17 @@ def test_dense_batch_overflow_scratch():
     got, _ = gpu_batch(pats, np.frombuffer(text, np.uint8), seg)
     assert np.array_equal(got, exp)
 
+
+
+def test_segments_not_covering_the_whole_buffer():
+    # bytes before the first segment and after the last one belong to no segment; empty segments anywhere
+    rnd = random.Random(5)
+    text = bytes(rnd.choice(b"abcab") for _ in range(300_000))
+    cuts = sorted(rnd.sample(range(5000, 290_000), 400))
+    cuts += [cuts[10], cuts[10], cuts[200]]  # empty segments
+    seg = np.array(sorted([3001] + cuts + [290_000, 290_000]), np.uint64)
+    pats = [b"abca", b"cab", b"bcabc", b"aaaa", b"b"]
+    exp = oracle.batch(text, seg, pats, method="naive")
+    got, n = gpu_batch(pats, np.frombuffer(text, np.uint8), seg)
+    assert n == len(exp)
+    assert np.array_equal(got, exp)
