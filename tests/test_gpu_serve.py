@@ -30,6 +30,9 @@ def _solo(sets, reqs):
     out = []
     for r in reqs:
         a = autos.setdefault(r.set_index, glop.Automaton(sets[r.set_index]))
+        if r.payload.numel() == 0:
+            out.append(np.zeros((0, 2), np.uint32))
+            continue
         m, n = a.scan(r.payload.cuda())
         out.append(m.cpu().numpy().view(np.uint32))
     return out
@@ -85,3 +88,24 @@ def test_results_larger_than_pinned_buffer_and_rescans():
     for r, e in zip(reqs, exp):
         assert r.count == len(e), r.rid
         assert np.array_equal(r.matches, e), r.rid
+
+
+def test_empty_and_tiny_requests():
+    sets = W.config5_sets()[:2]
+    reqs = _requests(24)
+    empty = torch.empty(0, dtype=torch.uint8).pin_memory()
+    for k, r in enumerate(reqs):
+        r.set_index %= 2
+        if k % 5 == 0:
+            r.payload = empty
+        elif k % 5 == 1:
+            r.payload = r.payload[:3]
+    exp = _solo(sets, [r for r in reqs])
+    for realtime in (True, False):
+        srv = serve.BatchServer(sets, hbm_budget=1 << 30, keep_matches=True)
+        for r in reqs:
+            r.count, r.matches, r.done = -1, None, -1.0
+        srv.serve(reqs, realtime=realtime)
+        for r, e in zip(reqs, exp):
+            assert r.count == len(e), (realtime, r.rid)
+            assert np.array_equal(r.matches.reshape(-1, 2), e.reshape(-1, 2)), (realtime, r.rid)

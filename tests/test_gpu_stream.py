@@ -51,3 +51,17 @@ def test_small_output_buffer_rescans_and_prefix_mode():
     exp = oracle.ac_mt(w.text, w.patterns.csr(), prefix_len=8).astype(np.uint64)
     assert np.array_equal(got, exp)
     assert sc.stats["rescans"] > 0
+
+
+def test_empty_and_one_byte_chunks():
+    w = W.config2(2 * W.MiB + 5)
+    cuts, left, k = [], w.text.size, 0
+    while left:
+        c = min(left, [0, 1, 0, 65536, 1, 300000][k % 6])
+        cuts.append(c)
+        left -= c
+        k += 1
+    sc = StreamScanner(w.patterns, chunk_bytes=1 << 20, out_rows=1 << 18)
+    got = _stream(sc, w.text, cuts)
+    exp = oracle.ac_mt(w.text, w.patterns.csr()).astype(np.uint64)
+    assert np.array_equal(got, exp)
