@@ -104,6 +104,49 @@ def read_stream_peak(dev, nbytes: int = 4 << 30, reps: int = 10):
     return round(gbs, 1)
 
 
+def link_roofline(host, staging, hm_pinned, N: int, M: int, step_s: float, reps: int = 10):
+    """The host link's floor for one end-to-end step: plain copies of the step's bytes (the text up from the
+    same pinned buffer, the matches down into the same pinned buffer), each alone and both at once on two
+    streams; frac = that floor / the measured end-to-end step."""
+    import torch
+    dev = staging.device
+    up_s, down_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    d_text = staging[:N]
+    d_out = staging[N:N + 8 * M] if staging.numel() >= N + 8 * M else torch.empty(8 * M, dtype=torch.uint8, device=dev)
+    h_out = hm_pinned.view(torch.uint8).reshape(-1)[:8 * M]
+
+    def up():
+        with torch.cuda.stream(up_s):
+            d_text.copy_(host[:N], non_blocking=True)
+
+    def down():
+        with torch.cuda.stream(down_s):
+            h_out.copy_(d_out, non_blocking=True)
+
+    def both():
+        up()
+        down()
+
+    def timed(fn):
+        best = float("inf")
+        for _ in range(3):
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize()
+            best = min(best, (time.perf_counter() - t0) / reps)
+        return best
+
+    tu, td, tb = timed(up), timed(down), timed(both)
+    return {"h2d_GBps": round(N / tu / 1e9, 1), "d2h_GBps": round(8 * M / td / 1e9, 1),
+            "h2d_ms": round(tu * 1e3, 3), "d2h_ms": round(td * 1e3, 3), "both_ms": round(tb * 1e3, 3),
+            "e2e_ms": round(step_s * 1e3, 3), "frac": round(tb / step_s, 4),
+            "note": "plain cudaMemcpyAsync of the step's bytes from/to the same pinned buffers (best of 3 x %d); "
+                    "frac = both copies at once / end-to-end step" % reps}
+
+
 def walk_stats(w, sample_bytes: int = 8 << 20):
     """Walk counters of the scan's decision rules on the first sample_bytes of the workload (whole
     segments for batches), from the library's host walk emulation: start-filter pass rate, gram-table
@@ -340,8 +383,9 @@ def run_prefix_fp(args, ws, rank):
 
 def run_stream(args, ws, rank):
     """Streaming ingestion of config 2 (256 MiB syslog, 1,000 patterns) from pinned host memory in 16 MiB
-    chunks: the two-slot StreamScanner (uploads under scans, halo carried on the device) against the same
-    chunks scanned one after another through glop_scan_host, and against one glop_scan_host call."""
+    chunks: the StreamScanner (three slots: upload and scan of one chunk under the copy-back of the previous
+    one; halo carried on the device), against its two-slot form and against the same chunks scanned one after
+    another through glop_scan_host."""
     if rank != 0:
         return
     import ctypes
@@ -359,27 +403,30 @@ def run_stream(args, ws, rank):
     host = torch.from_numpy(w.text).pin_memory()
     chunks = [host[i:i + chunk] for i in range(0, N, chunk)]
     a = glop.Automaton(w.patterns)
-    sc = StreamScanner(a, chunk_bytes=chunk, out_rows=8 << 20)
 
-    def streamed():
-        n = 0
-        for c in chunks:
-            n += len(sc.feed(c))
-        return n + len(sc.flush())
+    def timed_stream(depth):
+        sc = StreamScanner(a, chunk_bytes=chunk, out_rows=8 << 20, depth=depth)
 
-    def fresh():
-        sc.pos = sc.buf_start = sc.k = 0
-        sc.tail_len = 0
-        sc.tail_slot = None
+        def streamed():
+            n = 0
+            for c in chunks:
+                n += len(sc.feed(c))
+            return n + sum(len(r) for r in sc.flush())
 
-    M = streamed()
-    times = []
-    for _ in range(max(args.steps, 3)):
-        fresh()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        assert streamed() == M
-        times.append(time.perf_counter() - t0)
+        m = streamed()
+        times = []
+        for _ in range(max(args.steps, 3)):
+            sc.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            assert streamed() == m
+            times.append(time.perf_counter() - t0)
+        sc.close()
+        return m, times
+
+    M, times = timed_stream(2)
+    M1, times1 = timed_stream(1)
+    assert M1 == M
     # the same chunks, one glop_scan_host call after another (each copies in, scans and copies back)
     halo = a.info["max_pattern_len"] - 1
     need = ctypes.c_uint64()
@@ -399,12 +446,13 @@ def run_stream(args, ws, rank):
                                            st.cuda_stream)
             assert rc == 0, rc
         ser.append(time.perf_counter() - t0)
-    tm, ts = statistics.median(times), statistics.median(ser)
+    tm, ts, t1 = statistics.median(times), statistics.median(ser), statistics.median(times1)
     line = {"metric": "Gbit/s ingested from a host stream (8*N/t, Eq. 1)", "value": round(8.0 * N / tm / 1e9, 3),
             "unit": "Gbit/s", "n_gpus": 1, "steps": len(times), "warmup": 1, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "stream-256MiB-1000pat", "chunk_bytes": chunk, "matches": int(M)},
-            "stream": {"two_slot_s": round(tm, 4), "serial_glop_scan_host_s": round(ts, 4),
+            "stream": {"depth": 2, "depth2_s": round(tm, 4), "depth1_s": round(t1, 4),
+                       "depth1_gbps": round(8.0 * N / t1 / 1e9, 3), "serial_glop_scan_host_s": round(ts, 4),
                        "serial_gbps": round(8.0 * N / ts / 1e9, 3),
                        "note": "timed from the first chunk fed to the last match in host memory (the owned rows of each "
                 "chunk, pinned, relative to the chunk's base)"}}
@@ -677,6 +725,8 @@ def main():
         dt = time.perf_counter() - t0
         e2e = {"value": round(8.0 * N * args.e2e_steps * ws / dt / 1e9, 3), "unit": "Gbit/s",
                "h2d_bytes_per_step": N, "d2h_bytes_per_step": 8 + 8 * M}
+        if not args.no_extras:
+            e2e["link"] = link_roofline(host, staging, hm_pinned, N, M, dt / args.e2e_steps)
         del hm, need
 
     if rank != 0:

@@ -191,6 +191,23 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
                            glop_stream_t stream);
 
 /*
+ * glop_scan_host_plan -- the pieces glop_scan_host splits a len-byte text
+ * into (the paper's overlap of the next batch's transfer with the current
+ * scan, Sec. 6): piece k is bytes [bounds[k], bounds[k + 1]) for
+ * k < *n_pieces, with bounds[0] = 0, bounds[*n_pieces] = len, strictly
+ * increasing, inner bounds multiples of 4096.  Texts under 64 MiB go in one
+ * piece; longer ones in at most 9: a short first piece, then equal full
+ * pieces (8 at most, and at most one per 32 MiB of text).
+ * (glop_scan_host scans an automaton without patterns in one piece whatever
+ * the length.)  Each piece's scan also reads the next longest-pattern - 1
+ * bytes; its upload is issued with them.  Host only, no device work.
+ * bounds (caller-owned, may be NULL to query *n_pieces alone) must hold
+ * *n_pieces + 1 entries: max_bounds smaller returns GLOP_EINVAL with
+ * *n_pieces set.
+ */
+glop_status glop_scan_host_plan(uint64_t len, uint64_t *bounds, uint32_t max_bounds, uint32_t *n_pieces);
+
+/*
  * glop_tune -- pick compile options for a pattern set by timing scans of a
  * sample on the current device: the start filter's gram length and bitmap
  * size and the shared-memory budget of on-chip transition rows.  Every

@@ -283,12 +283,35 @@ glop_status glop_scan_host_staging_size(glop_handle h, uint64_t len, uint64_t ca
 
 namespace {
 
-// glop_scan_host on long texts: pieces of at least kPieceMin bytes, uploaded on one stream, scanned in order
-// on the caller's stream (each scan places its matches after the previous piece's, from a device word, and
-// covers the next longest-pattern - 1 bytes as look-ahead), and copied back on a third stream as soon as each
-// piece's count is known -- uploads, scans and copy-backs of different pieces overlap.
+// glop_scan_host on long texts: pieces uploaded on one stream, scanned in order on the caller's stream (each
+// scan places its matches after the previous piece's, from a device word, and covers the next
+// longest-pattern - 1 bytes as look-ahead), and copied back on a third stream as soon as each piece's count is
+// known -- uploads, scans and copy-backs of different pieces overlap.  A first piece of 1/kHeadDiv of a full
+// one (the copy-back of the first matches starts after a short upload and scan), then up to kMidPieces equal
+// full pieces, at most one per kPieceMin bytes.  kTailDiv > 0 would end on a short piece as well; on GB300 that
+// measured no faster (the copy-back, not the last scan, ends the call).
 constexpr uint64_t kPieceMin = 32ull << 20;
-constexpr uint32_t kMaxPieces = 8;
+constexpr uint32_t kMidPieces = 8;
+constexpr uint32_t kHeadDiv = 4, kTailDiv = 0;  // 0: no short piece at that end
+constexpr uint32_t kMaxPieces = kMidPieces + 2;
+constexpr uint64_t kCopyAlign = 4096;
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Piece boundaries of a len-byte text (len >= 2 * kPieceMin): bnd[0] = 0 < bnd[1] < ... < bnd[P] = len, every
+// inner boundary a multiple of kCopyAlign.  Returns P.
+uint32_t piece_plan(uint64_t len, uint64_t *bnd) {
+    const uint32_t M = (uint32_t)std::min<uint64_t>(kMidPieces, len / kPieceMin);
+    const double w = M + (kHeadDiv ? 1.0 / kHeadDiv : 0.0) + (kTailDiv ? 1.0 / kTailDiv : 0.0);
+    const uint64_t ps = round_up((uint64_t)((double)len / w) + 1, kCopyAlign);
+    uint32_t P = 0;
+    uint64_t b = 0;
+    bnd[0] = 0;
+    if constexpr (kHeadDiv != 0) bnd[++P] = b = std::min(len, round_up(ps / kHeadDiv, kCopyAlign));
+    for (uint32_t i = 0; i < M && b < len; ++i) bnd[++P] = b = std::min(len, b + ps);
+    if (b < len) bnd[++P] = len;
+    return P;
+}
 
 static_assert((2 * kMaxPieces + 1) * 8 <= 512, "per-piece counts and bases fit the count area");
 
@@ -322,22 +345,29 @@ glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len,
                              void *ws, uint64_t ws_bytes, cudaStream_t st) {
     HostPipe *hp = host_pipe(h->device);
     if (!hp) return GLOP_ECUDA;
-    const uint32_t P = (uint32_t)std::min<uint64_t>(kMaxPieces, len / kPieceMin);
-    const uint64_t ps = ((len + P - 1) / P + 1023) / 1024 * 1024;
+    uint64_t bnd[kMaxPieces + 1];
+    const uint32_t P = piece_plan(len, bnd);
     const uint64_t halo = h->dev.max_len ? h->dev.max_len - 1 : 0;
     uint64_t *d_counts = d_c, *d_bases = d_c + kMaxPieces;  // count area: P counts, P + 1 bases
-    auto lo = [&](uint32_t k) { return std::min<uint64_t>(len, k * ps); };
+    auto lo = [&](uint32_t k) { return bnd[k]; };
+    // upload k covers [up_lo(k), up_lo(k + 1)): piece k's bytes from the end of the previous piece's look-ahead
+    // through its own look-ahead, so scan k waits for upload k alone (earlier uploads precede it on `up`).
+    // The look-ahead end is rounded up to kCopyAlign bytes, so every copy starts aligned.
+    auto up_lo = [&](uint32_t k) -> uint64_t {
+        if (k == 0) return 0;
+        if (k >= P) return len;
+        return std::min(len, round_up(lo(k) + halo, kCopyAlign));
+    };
     if (cudaMemsetAsync(d_bases, 0, 8, st) != cudaSuccess) return GLOP_ECUDA;
     for (uint32_t k = 0; k < P; ++k) {
-        const uint64_t a = lo(k), b = lo(k + 1);
+        const uint64_t a = up_lo(k), b = up_lo(k + 1);
         if (b > a && cudaMemcpyAsync(d_text + a, h_text + a, b - a, cudaMemcpyHostToDevice, hp->up) != cudaSuccess)
             return GLOP_ECUDA;
         if (cudaEventRecord(hp->uploaded[k], hp->up) != cudaSuccess) return GLOP_ECUDA;
     }
     for (uint32_t k = 0; k < P; ++k) {
         const uint64_t a = lo(k), b = lo(k + 1), e = std::min(len, b + halo);
-        for (uint32_t q = k; q < P && lo(q) < std::max(e, b); ++q)  // this piece and its look-ahead
-            if (cudaStreamWaitEvent(st, hp->uploaded[q], 0) != cudaSuccess) return GLOP_ECUDA;
+        if (cudaStreamWaitEvent(st, hp->uploaded[k], 0) != cudaSuccess) return GLOP_ECUDA;
         glop::ScanLaunch L;
         L.A = &h->dev;
         L.text = d_text + a;
@@ -375,8 +405,13 @@ glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len,
         const uint64_t c = hp->pinned[2 * k];
         flags |= (uint32_t)hp->pinned[2 * k + 1];
         const uint64_t n = base < capacity ? std::min(c, capacity - base) : 0;
+        // the copy starts on a kCopyAlign boundary of the output: the bytes before this piece's first match are
+        // earlier pieces' matches, final on the device and copied again unchanged after their own copy
+        const uint64_t c0 = base * sizeof(glop_match) / kCopyAlign * kCopyAlign;
+        const uint64_t c1 = (base + n) * sizeof(glop_match);
         if (n && (cudaStreamWaitEvent(hp->down, hp->scanned[k], 0) != cudaSuccess ||
-                  cudaMemcpyAsync(h_matches + base, d_m + base, n * sizeof(glop_match), cudaMemcpyDeviceToHost,
+                  cudaMemcpyAsync(reinterpret_cast<uint8_t *>(h_matches) + c0,
+                                  reinterpret_cast<const uint8_t *>(d_m) + c0, c1 - c0, cudaMemcpyDeviceToHost,
                                   hp->down) != cudaSuccess))
             return GLOP_ECUDA;
         base += c;
@@ -390,6 +425,17 @@ glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len,
 }
 
 }  // namespace
+
+glop_status glop_scan_host_plan(uint64_t len, uint64_t *bounds, uint32_t max_bounds, uint32_t *n_pieces) {
+    if (!n_pieces) return GLOP_EINVAL;
+    uint64_t bnd[kMaxPieces + 1] = {0, len};
+    const uint32_t P = len >= 2 * kPieceMin ? piece_plan(len, bnd) : 1;
+    *n_pieces = P;
+    if (!bounds) return GLOP_OK;
+    if (max_bounds < P + 1) return GLOP_EINVAL;
+    for (uint32_t k = 0; k <= P; ++k) bounds[k] = bnd[k];
+    return GLOP_OK;
+}
 
 glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, glop_match *h_matches,
                            uint64_t capacity, uint64_t *h_count, void *d_staging, uint64_t staging_bytes,

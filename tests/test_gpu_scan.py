@@ -195,11 +195,15 @@ def test_scan_host_pieces_cross_boundaries_and_overflow():
     pats = W.Patterns.from_list(w.patterns.as_list() + [longp])
     text = w.text.copy()
     n = text.size
-    pieces = min(8, n // (32 << 20))
-    ps = ((n + pieces - 1) // pieces + 1023) // 1024 * 1024
-    bounds = list(range(ps, n, ps))
-    for b in bounds:  # one copy across each piece boundary
+    bounds = glop.host_plan(n)[1:-1]
+    assert len(bounds) >= 2
+    halo = len(longp) - 1
+    for b in bounds:
+        # one copy across each piece boundary, and one across the end of the previous piece's look-ahead
+        # (rounded up to 4096), where the upload of the next piece begins
+        up = (b + halo + 4095) // 4096 * 4096
         text[b - 100:b + 99] = np.frombuffer(longp, np.uint8)
+        text[up - 48:up + 151] = np.frombuffer(longp, np.uint8)
     exp = oracle.ac_mt(text, pats.csr())
     a = glop.Automaton(pats)
     pinned = torch.from_numpy(text).pin_memory().numpy()
@@ -207,7 +211,8 @@ def test_scan_host_pieces_cross_boundaries_and_overflow():
     assert total == len(exp)
     assert np.array_equal(got, exp)
     long_at = got[got[:, 1] == len(pats.as_list()) - 1][:, 0]
-    assert set(b - 100 for b in bounds) <= set(int(x) for x in long_at)
+    assert set(b - 100 for b in bounds) | set((b + halo + 4095) // 4096 * 4096 - 48 for b in bounds) <= set(
+        int(x) for x in long_at)
     cap = len(exp) // 2 + 7
     got2, total2 = a.scan_host(text, capacity=cap)
     assert total2 == len(exp)
