@@ -177,6 +177,22 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
 glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count);
 
 /*
+ * glop_scan_words -- queue, on stream, the copy of a finished scan's match
+ * count and status into pinned host memory, made by a one-thread kernel and
+ * not by the copy engine (a small device-to-host memcpy waits behind any
+ * large copy already in flight and holds up its stream).  d_workspace is the
+ * workspace of a glop_scan or glop_scan_batch queued earlier on stream;
+ * h_words (caller-owned, two uint64_t host words the device can address:
+ * pinned by cudaMallocHost / cudaHostAlloc / cudaHostRegister; on systems
+ * whose GPU reads host page tables, any host memory) receives [total match
+ * count, glop_status of the scan as glop_scan_status maps it].  The values
+ * are there once the stream has passed this point (an event or a
+ * synchronize).  GLOP_EINVAL when a pointer is NULL or the driver reports
+ * h_words as not addressable by the device.
+ */
+glop_status glop_scan_words(const void *d_workspace, uint64_t *h_words, glop_stream_t stream);
+
+/*
  * glop_scan_host -- glop_scan on HOST buffers, end to end: copies text to the
  * device, scans, copies the count and the matches back, and waits for
  * completion.  Device buffers come from d_staging (at least

@@ -37,7 +37,7 @@ SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_w
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
            "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc", "glop_plan_create",
            "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split",
-           "glop_count_workspace_size", "glop_scan_count", "glop_scan_host_plan"]
+           "glop_count_workspace_size", "glop_scan_count", "glop_scan_host_plan", "glop_scan_words"]
 
 
 class GlopError(RuntimeError):
@@ -110,6 +110,8 @@ def lib():
         L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
         L.glop_batch_split.restype = ctypes.c_int
         L.glop_batch_split.argtypes = [vp, vp, u64, ctypes.c_uint32, vp, vp, vp]
+        L.glop_scan_words.restype = ctypes.c_int
+        L.glop_scan_words.argtypes = [vp, vp, vp]
         L.glop_scan_host_plan.restype = ctypes.c_int
         L.glop_scan_host_plan.argtypes = [u64, vp, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]
         L.glop_count_workspace_size.restype = ctypes.c_int

@@ -318,7 +318,8 @@ static_assert((2 * kMaxPieces + 1) * 8 <= 512, "per-piece counts and bases fit t
 struct HostPipe {
     cudaStream_t up = nullptr, down = nullptr;
     cudaEvent_t uploaded[kMaxPieces] = {}, scanned[kMaxPieces] = {};
-    uint64_t *pinned = nullptr;  // per piece: match count, header flags
+    uint64_t *pinned = nullptr;  // per piece: match count, status (written by the words kernel)
+    unsigned long long *pinned_dev = nullptr;  // the same words as the device addresses them
     bool ok = false;
 };
 
@@ -330,7 +331,8 @@ HostPipe *host_pipe(int dev) {
     if (hp.ok) return &hp;
     if (cudaStreamCreateWithFlags(&hp.up, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&hp.down, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(&hp.pinned, 2 * kMaxPieces * sizeof(uint64_t)) != cudaSuccess)
+        cudaMallocHost(&hp.pinned, 2 * kMaxPieces * sizeof(uint64_t)) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&hp.pinned_dev), hp.pinned, 0) != cudaSuccess)
         return nullptr;
     for (uint32_t k = 0; k < kMaxPieces; ++k)
         if (cudaEventCreateWithFlags(&hp.uploaded[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -392,18 +394,20 @@ glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len,
         }
         const int rc = glop::launch_scan(L);
         if (rc) return (glop_status)rc;
-        if (cudaMemcpyAsync(hp->pinned + 2 * k, d_counts + k, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(hp->pinned + 2 * k + 1, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaEventRecord(hp->scanned[k], st) != cudaSuccess)
+        // the count and status reach the host through a kernel's stores: a memcpy would wait behind the
+        // previous piece's copy-back on the copy engine and hold up the next scan
+        if (glop::launch_words(ws, hp->pinned_dev + 2 * k, st) || cudaEventRecord(hp->scanned[k], st) != cudaSuccess)
             return GLOP_ECUDA;
     }
     uint64_t base = 0;
-    uint32_t flags = 0;
+    bool internal = false, timeout = false;
     for (uint32_t k = 0; k < P; ++k) {
         if (lo(k + 1) == lo(k)) continue;
         if (cudaEventSynchronize(hp->scanned[k]) != cudaSuccess) return GLOP_ECUDA;
         const uint64_t c = hp->pinned[2 * k];
-        flags |= (uint32_t)hp->pinned[2 * k + 1];
+        // (a piece's own overflow status is not used: the whole text's overflow is base > capacity below)
+        internal |= hp->pinned[2 * k + 1] == GLOP_EINTERNAL;
+        timeout |= hp->pinned[2 * k + 1] == GLOP_ETIMEOUT;
         const uint64_t n = base < capacity ? std::min(c, capacity - base) : 0;
         // the copy starts on a kCopyAlign boundary of the output: the bytes before this piece's first match are
         // earlier pieces' matches, final on the device and copied again unchanged after their own copy
@@ -418,8 +422,8 @@ glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len,
     }
     if (cudaStreamSynchronize(hp->down) != cudaSuccess) return GLOP_ECUDA;
     *h_count = base;
-    if (flags & glop::WS_INTERNAL) return GLOP_EINTERNAL;
-    if (flags & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
+    if (internal) return GLOP_EINTERNAL;
+    if (timeout) return GLOP_ETIMEOUT;
     if (base > capacity) return GLOP_EOVERFLOW;
     return GLOP_OK;
 }
@@ -461,22 +465,18 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
     if (len && cudaMemcpyAsync(d_text, h_text, len, cudaMemcpyHostToDevice, st) != cudaSuccess) return GLOP_ECUDA;
     glop_status s = glop_scan(h, d_text, len, d_m, capacity, d_c, ws, ws_bytes, stream);
     if (s != GLOP_OK) return s;
-    // the count and the status word come back together (the thread's pinned words): one round trip
+    // the count and the status come back together in the thread's pinned words (written by a kernel)
     HostPipe *hp = host_pipe(dev);
     if (!hp) return GLOP_ECUDA;
-    if (cudaMemcpyAsync(hp->pinned, d_c, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(hp->pinned + 1, ws, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return GLOP_ECUDA;
+    if (glop::launch_words(ws, hp->pinned_dev, st) || cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;
     const uint64_t total = hp->pinned[0];
-    const uint32_t hdr0 = (uint32_t)hp->pinned[1];
+    const uint64_t status = hp->pinned[1];
     *h_count = total;
     uint64_t n = total < capacity ? total : capacity;
     if (n && (cudaMemcpyAsync(h_matches, d_m, n * sizeof(glop_match), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
               cudaStreamSynchronize(st) != cudaSuccess))
         return GLOP_ECUDA;
-    if (hdr0 & glop::WS_INTERNAL) return GLOP_EINTERNAL;
-    if (hdr0 & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
+    if (status == GLOP_EINTERNAL || status == GLOP_ETIMEOUT) return (glop_status)status;
     if (total > capacity) return GLOP_EOVERFLOW;
     return GLOP_OK;
 }

@@ -87,3 +87,6 @@ def test_new_entry_points_reject_bad_arguments_before_any_device_work(libpath):
     p = ctypes.addressof(dummy)
     assert lib.glop_batch_split(None, p, 0, 0xFFFFFFFF, None, p, None) == glop.EINVAL
     assert lib.glop_batch_split(None, p, 5, 1, None, p, None) == glop.EINVAL  # capacity without arrays
+    # count and status words: NULL workspace or words
+    assert lib.glop_scan_words(None, p, None) == glop.EINVAL
+    assert lib.glop_scan_words(p, None, None) == glop.EINVAL

@@ -146,6 +146,35 @@ def test_overflow_reports_true_count():
     a.close()
 
 
+def test_scan_words_count_and_status_in_pinned_memory():
+    # glop_scan_words writes the scan's count and status into pinned host words with a kernel
+    w = W.config1()
+    exp = oracle.ac(w.text, w.patterns.csr())
+    a = glop.Automaton(w.patterns)
+    L = glop.lib()
+    st = torch.cuda.Stream()
+    words = torch.zeros(2, dtype=torch.int64, pin_memory=True)
+    for cap, status in ((len(exp) + 5, glop.OK), (len(exp) // 3, glop.EOVERFLOW)):
+        d = _dev(w.text)
+        ws = a.workspace(d.numel(), d.device)
+        m = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        words.fill_(-1)
+        a.scan_into(d, m, cnt, workspace=ws, stream=st)
+        assert L.glop_scan_words(ws.data_ptr(), words.data_ptr(), st.cuda_stream) == glop.OK
+        st.synchronize()
+        assert words.tolist() == [len(exp), status]
+        assert a.status(d.device, stream=st) == status
+    # an empty text: count 0, OK
+    e = torch.empty(0, dtype=torch.uint8, device="cuda")
+    ws = a.workspace(0, e.device)
+    a.scan_into(e, None, cnt, workspace=ws, stream=st)
+    assert L.glop_scan_words(ws.data_ptr(), words.data_ptr(), st.cuda_stream) == glop.OK
+    st.synchronize()
+    assert words.tolist() == [0, glop.OK]
+    a.close()
+
+
 def test_config1_full_both_oracles():
     w = W.config1()
     got, n = gpu_scan(w.patterns, w.text)
