@@ -193,6 +193,50 @@ glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint
 glop_status glop_scan_words(const void *d_workspace, uint64_t *h_words, glop_stream_t stream);
 
 /*
+ * glop_ingest_* -- a byte stream scanned chunk by chunk as it arrives (the
+ * paper streams the next batch to the GPU while the current one is scanned,
+ * Sec. 6), with the uploads, scans and copy-backs of consecutive chunks
+ * overlapped.  Each scan covers the carried last longest-pattern - 1 bytes of
+ * the previous buffer (kept on the device) plus the new chunk, and owns the
+ * match starts before its last longest-pattern - 1 bytes (the final scan owns
+ * all of them); in order, the results are exactly the matches of the whole
+ * stream, with offsets relative to each result's base.
+ *
+ * glop_ingest_create: chunks of at most chunk_bytes; out_rows the initial
+ * match rows per chunk (0: a quarter of the chunk; more matches are handled
+ * by scanning the chunk again into a larger output); depth (1 ..
+ * GLOP_INGEST_MAX_DEPTH) the number of chunks whose results are not handed
+ * out yet.  Allocates depth + 1 slots (device buffers, pinned host rows,
+ * CUDA streams) on the current device, which must stay current for every
+ * call.  The handle h must outlive the object.
+ * glop_ingest_feed: queues n bytes of h_chunk (host memory; pinned is
+ * fastest; it must stay unchanged until the next feed or flush returns) and
+ * sets *res to the owned matches of the chunk fed depth calls before (count
+ * 0 while fewer were fed).  res->matches points into the object's pinned
+ * memory and stays valid until the second feed after the one that returned
+ * it.  Blocks until the previous chunk's scan has finished.
+ * glop_ingest_flush: ends the stream; res[0 .. *n_res) receive the results
+ * not handed out yet, in order (at most depth; max_res smaller returns
+ * GLOP_EINVAL with *n_res set).  glop_ingest_reset then starts a new stream.
+ * Errors from the scans (GLOP_ETIMEOUT, GLOP_EINTERNAL, GLOP_ECUDA) leave the
+ * object unusable: destroy it.  Not thread-safe: one thread per object.
+ */
+#define GLOP_INGEST_MAX_DEPTH 8
+typedef struct glop_ingest_s *glop_ingest; /* opaque */
+typedef struct {
+    uint64_t base;              /* stream offset that match offsets are relative to */
+    const glop_match *matches;  /* count rows, sorted by (offset, pattern_id) */
+    uint64_t count;
+} glop_ingest_result;
+glop_status glop_ingest_create(glop_handle h, uint64_t chunk_bytes, uint64_t out_rows, uint32_t depth,
+                               glop_ingest *out);
+glop_status glop_ingest_feed(glop_ingest s, const uint8_t *h_chunk, uint64_t n, glop_ingest_result *res);
+glop_status glop_ingest_flush(glop_ingest s, glop_ingest_result *res, uint32_t max_res, uint32_t *n_res);
+glop_status glop_ingest_reset(glop_ingest s);
+glop_status glop_ingest_info(glop_ingest s, uint64_t *chunks, uint64_t *rescans);
+glop_status glop_ingest_destroy(glop_ingest s);
+
+/*
  * glop_scan_host -- glop_scan on HOST buffers, end to end: copies text to the
  * device, scans, copies the count and the matches back, and waits for
  * completion.  Device buffers come from d_staging (at least

@@ -37,7 +37,14 @@ SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_w
            "glop_batch_workspace_size", "glop_scan_batch", "glop_scan_status", "glop_scan_host_staging_size",
            "glop_scan_host", "glop_destroy", "glop_status_str", "glop_scan_noalloc", "glop_plan_create",
            "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split",
-           "glop_count_workspace_size", "glop_scan_count", "glop_scan_host_plan", "glop_scan_words"]
+           "glop_count_workspace_size", "glop_scan_count", "glop_scan_host_plan", "glop_scan_words",
+           "glop_ingest_create", "glop_ingest_feed", "glop_ingest_flush", "glop_ingest_reset", "glop_ingest_info",
+           "glop_ingest_destroy"]
+
+
+class IngestResult(ctypes.Structure):
+    """glop_ingest_result: base stream offset, pointer to count (offset, pattern_id) rows, count."""
+    _fields_ = [("base", ctypes.c_uint64), ("matches", ctypes.c_void_p), ("count", ctypes.c_uint64)]
 
 
 class GlopError(RuntimeError):
@@ -110,6 +117,15 @@ def lib():
         L.glop_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, vp, vp]
         L.glop_batch_split.restype = ctypes.c_int
         L.glop_batch_split.argtypes = [vp, vp, u64, ctypes.c_uint32, vp, vp, vp]
+        for name, args in (("glop_ingest_create", [vp, u64, u64, ctypes.c_uint32, ctypes.POINTER(vp)]),
+                           ("glop_ingest_feed", [vp, vp, u64, ctypes.POINTER(IngestResult)]),
+                           ("glop_ingest_flush", [vp, ctypes.POINTER(IngestResult), ctypes.c_uint32,
+                                                  ctypes.POINTER(ctypes.c_uint32)]),
+                           ("glop_ingest_reset", [vp]),
+                           ("glop_ingest_info", [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+                           ("glop_ingest_destroy", [vp])):
+            getattr(L, name).restype = ctypes.c_int
+            getattr(L, name).argtypes = args
         L.glop_scan_words.restype = ctypes.c_int
         L.glop_scan_words.argtypes = [vp, vp, vp]
         L.glop_scan_host_plan.restype = ctypes.c_int

@@ -13,20 +13,20 @@ pattern - 1 bytes.  Here:
   ``flush`` owns everything up to the end of the stream.  The owned matches
   are a prefix of the scan's sorted output;
 * ``depth + 1`` slots, each with its own CUDA stream, device buffers and
-  pinned result buffer, rotate: one chunk's host-to-device copy and scan run
-  while the previous chunk's matches are copied back and the host hands out
-  the results of the one before, in stream order.
+  pinned result rows, rotate: one chunk's host-to-device copy and scan run
+  while the previous chunk's matches are copied back and the results of the
+  one before are handed out, in stream order.
 
-All matching runs in the library's kernels (``glop_scan``); this module
-moves bytes and keeps the books.
+The engine is native (``glop_ingest_*`` in the C ABI) and this module wraps
+it; ``owned_end`` states the ownership rule the engine applies.
 """
 from __future__ import annotations
 
-import bisect
+import ctypes
 
 import numpy as np
 
-from . import Automaton, GlopError, OK, lib
+from . import Automaton, GlopError, IngestResult, OK, lib
 
 
 def owned_end(buf_start: int, buf_end: int, halo: int, final: bool) -> int:
@@ -53,30 +53,17 @@ class StreamResult:
         return out
 
 
-_EMPTY = StreamResult(0, np.zeros((0, 2), np.uint32))
+_NONE = np.zeros((0, 2), np.uint32)
 
 
-class _Slot:
-    def __init__(self, torch, device, cap_bytes: int, out_rows: int, ws_bytes: int):
-        self.stream = torch.cuda.Stream(device=device)
-        self.text = torch.empty(cap_bytes, dtype=torch.uint8, device=device)
-        self.out = torch.empty((out_rows, 2), dtype=torch.int32, device=device)
-        self.count = torch.zeros(1, dtype=torch.int64, device=device)
-        self.ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
-        self.count_host = torch.empty(1, dtype=torch.int64, pin_memory=True)
-        self.out_host = torch.empty((out_rows, 2), dtype=torch.int32, pin_memory=True)
-        self.last_len = 0
-        self.uploaded = torch.cuda.Event()  # the chunk's bytes are on the device
-        self.done = torch.cuda.Event()      # the scan and its match count's copy-back finished
-        self.copied = torch.cuda.Event()    # the scan's matches are in out_host
+class _Same:
+    """No device change (a context manager that does nothing)."""
 
+    def __enter__(self):
+        return self
 
-class _Pending:
-    """A queued scan whose results have not been returned: stream bytes [b0, b1) in ``slot``."""
-
-    def __init__(self, slot, b0: int, b1: int):
-        self.slot, self.b0, self.b1 = slot, b0, b1
-        self.n = -1  # match count, once the scan is over and its copy-back is queued
+    def __exit__(self, *exc):
+        return False
 
 
 class StreamScanner:
@@ -84,136 +71,87 @@ class StreamScanner:
 
     ``feed(chunk)`` queues the chunk and returns the results of the chunk fed ``depth`` calls before it (an
     empty result while fewer were fed); ``flush()`` returns the rest, as a list.  Each result is a
-    StreamResult; in order, their matches are exactly the matches of the whole stream.  ``depth + 1`` slots
-    rotate: with ``depth`` = 2, one chunk uploads and scans while the previous chunk's matches copy back and
-    the one before is handed out, so the host's own work overlaps the device's."""
+    StreamResult; in order, their matches are exactly the matches of the whole stream.  A chunk must stay
+    unchanged until the next ``feed`` (or ``flush``) returns; the scanner keeps a reference to it."""
 
     def __init__(self, patterns, chunk_bytes: int = 16 << 20, out_rows: int | None = None, prefix_len: int = 0,
                  device=None, depth: int = 2):
-        import torch
-        self.torch = torch
-        self.device = torch.device(device or "cuda")
-        self.a = patterns if isinstance(patterns, Automaton) else Automaton(patterns, prefix_len=prefix_len)
-        self.halo = max(int(self.a.info["max_pattern_len"]) - 1, 0)
+        # the engine works on the device current at creation; `device` makes it current for every call
+        self._ctx = None
+        if device is not None:
+            import torch
+            self._ctx = torch.cuda.device(device)
         self.chunk_bytes = chunk_bytes
-        self.depth = max(1, int(depth))
-        cap = chunk_bytes + self.halo
-        rows = out_rows if out_rows is not None else max(1 << 16, cap // 4)
-        ws = self.a.workspace_bytes(cap)
-        self.slots = [_Slot(torch, self.device, cap, rows, ws) for _ in range(self.depth + 1)]
+        self.depth = int(depth)
         self.lib = lib()
-        self.stats = {"chunks": 0, "rescans": 0}
-        self.reset()
-
-    def reset(self):
-        """Start a new stream (the previous one must have been flushed)."""
-        self.pos = 0          # stream bytes fed so far
-        self.buf_start = 0    # stream offset of the next scan's buffer start
-        self.k = 0            # chunks fed
-        self.pending = []     # queued scans whose results are not yet returned, oldest first
-        self.tail_slot = None  # slot whose device buffer ends with the bytes to carry
-        self.tail_len = 0
-
-    def _start_copy(self, e: _Pending):
-        """Wait for the scan of e, then queue the copy-back of exactly its matches."""
-        torch = self.torch
-        s = e.slot
-        s.done.synchronize()
-        n = int(s.count_host.item())
-        if n > s.out.shape[0]:
-            # more matches than the output holds: scan the same buffer again into a larger one
-            self.stats["rescans"] += 1
-            s.out = torch.empty((n, 2), dtype=torch.int32, device=self.device)
-            self._scan(s, e.b1 - e.b0)
-            s.done.synchronize()
-        if s.out_host.shape[0] < n:
-            s.out_host = torch.empty((n, 2), dtype=torch.int32, pin_memory=True)
-        if n:
-            with torch.cuda.stream(s.stream):
-                s.out_host[:n].copy_(s.out[:n], non_blocking=True)
-        s.copied.record(s.stream)
-        e.n = n
-
-    def _finish(self, e: _Pending, final: bool) -> StreamResult:
-        """Wait for the copy-back of e and return its owned matches."""
-        if e.n < 0:
-            self._start_copy(e)
-        s = e.slot
-        s.copied.synchronize()
-        n = e.n
-        m = s.out_host[:n].numpy().view(np.uint32)
-        end = owned_end(e.b0, e.b1, self.halo, final) - e.b0
-        # first row at or past the owned end (binary search on the strided column, no copy of it)
-        col = m[:, 0]
-        keep = bisect.bisect_left(range(n), end, key=lambda i: int(col[i]))
-        return StreamResult(e.b0, m[:keep])
-
-    def _scan(self, s, nbytes: int):
-        torch = self.torch
-        rc = self.lib.glop_scan(self.a.handle, s.text.data_ptr(), nbytes, s.out.data_ptr(), s.out.shape[0],
-                                s.count.data_ptr(), s.ws.data_ptr(), s.ws.numel(), s.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        with self._ctx or _Same():
+            self.a = patterns if isinstance(patterns, Automaton) else Automaton(patterns, prefix_len=prefix_len)
+            rc = self.lib.glop_ingest_create(self.a.handle, chunk_bytes, out_rows or 0, self.depth, ctypes.byref(h))
+        self.halo = max(int(self.a.info["max_pattern_len"]) - 1, 0)
         if rc != OK:
-            raise GlopError(rc, "glop_scan")
-        with torch.cuda.stream(s.stream):
-            s.count_host.copy_(s.count, non_blocking=True)
-        s.done.record(s.stream)
+            raise GlopError(rc, "glop_ingest_create")
+        self._h = h
+        self._res = IngestResult()
+        self._hold = []  # the chunks whose uploads may still be running
+
+    @property
+    def stats(self) -> dict:
+        chunks, rescans = ctypes.c_uint64(), ctypes.c_uint64()
+        self.lib.glop_ingest_info(self._h, ctypes.byref(chunks), ctypes.byref(rescans))
+        return {"chunks": chunks.value, "rescans": rescans.value}
+
+    @staticmethod
+    def _result(r: IngestResult) -> StreamResult:
+        n = int(r.count)
+        if n == 0:
+            return StreamResult(int(r.base), _NONE)
+        rows = np.frombuffer((ctypes.c_uint32 * (2 * n)).from_address(r.matches), dtype=np.uint32)
+        return StreamResult(int(r.base), rows.reshape(n, 2))
 
     def feed(self, chunk) -> StreamResult:
         """Queue the next chunk (uint8 numpy array or CPU tensor, at most chunk_bytes); return the owned
         matches of the chunk fed ``depth`` calls before."""
-        torch = self.torch
-        t = chunk if isinstance(chunk, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(chunk, np.uint8))
-        n = t.numel()
+        if isinstance(chunk, np.ndarray):
+            buf = np.ascontiguousarray(chunk, dtype=np.uint8).reshape(-1)
+            ptr, n = buf.ctypes.data, buf.size
+        else:  # a CPU tensor
+            buf = chunk if chunk.is_contiguous() else chunk.contiguous()
+            ptr, n = buf.data_ptr(), buf.numel()
         if n > self.chunk_bytes:
             raise GlopError(1, "chunk of %d bytes > chunk_bytes %d" % (n, self.chunk_bytes))
-        nslot = len(self.slots)
-        s = self.slots[self.k % nslot]
-        prev = self.slots[(self.k - 1) % nslot]
-        h = self.tail_len
-        with torch.cuda.stream(s.stream):
-            if self.k:
-                # every earlier upload, and the tail copy that read this slot's old bytes, come first (each
-                # upload waits for the one before it)
-                s.stream.wait_event(prev.uploaded)
-            if h:
-                # the carried bytes: the end of the previous buffer
-                p = self.tail_slot
-                s.text[:h].copy_(p.text[p.last_len - h:p.last_len], non_blocking=True)
-            s.text[h:h + n].copy_(t, non_blocking=True)
-        s.uploaded.record(s.stream)
-        s.last_len = h + n
-        b0 = self.buf_start
-        b1 = b0 + h + n
-        # queue this chunk's scan, then, while it runs, queue the previous scan's copy-back and hand out the
-        # results of the chunk fed `depth` calls ago
-        self._scan(s, h + n)
-        self.pending.append(_Pending(s, b0, b1))
-        if len(self.pending) >= 2 and self.pending[-2].n < 0:
-            self._start_copy(self.pending[-2])
-        out = self._finish(self.pending.pop(0), final=False) if len(self.pending) > self.depth else _EMPTY
-        # next buffer starts where this scan's ownership ends
-        nxt = owned_end(b0, b1, self.halo, False)
-        self.tail_len = b1 - nxt
-        self.tail_slot = s
-        self.buf_start = nxt
-        self.pos += n
-        self.k += 1
-        self.stats["chunks"] += 1
-        return out
+        with self._ctx or _Same():
+            rc = self.lib.glop_ingest_feed(self._h, ptr if n else None, n, ctypes.byref(self._res))
+        if rc != OK:
+            raise GlopError(rc, "glop_ingest_feed")
+        self._hold = [self._hold[-1], buf] if self._hold else [buf]
+        return self._result(self._res)
 
     def flush(self) -> list:
         """Finish the stream: the results of every chunk not yet returned, in order; the last scan owns every
         remaining start."""
-        for e in self.pending:
-            if e.n < 0:
-                self._start_copy(e)
-        out = []
-        while self.pending:
-            e = self.pending.pop(0)
-            out.append(self._finish(e, final=not self.pending))
-        return out
+        res = (IngestResult * max(self.depth, 1))()
+        got = ctypes.c_uint32()
+        with self._ctx or _Same():
+            rc = self.lib.glop_ingest_flush(self._h, res, len(res), ctypes.byref(got))
+        if rc != OK:
+            raise GlopError(rc, "glop_ingest_flush")
+        self._hold = []
+        return [self._result(res[i]) for i in range(got.value)]
+
+    def reset(self):
+        """Start a new stream (the previous one must have been flushed)."""
+        rc = self.lib.glop_ingest_reset(self._h)
+        if rc != OK:
+            raise GlopError(rc, "glop_ingest_reset (flush first)")
 
     def close(self):
-        for s in self.slots:
-            s.done.synchronize()
-            s.copied.synchronize()
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.glop_ingest_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -90,3 +90,17 @@ def test_new_entry_points_reject_bad_arguments_before_any_device_work(libpath):
     # count and status words: NULL workspace or words
     assert lib.glop_scan_words(None, p, None) == glop.EINVAL
     assert lib.glop_scan_words(p, None, None) == glop.EINVAL
+    # streaming ingestion: NULL handle or output, depth out of range, NULL object
+    h = ctypes.c_void_p()
+    assert lib.glop_ingest_create(None, 1 << 20, 0, 2, ctypes.byref(h)) == glop.EINVAL and not h.value
+    assert lib.glop_ingest_create(p, 1 << 20, 0, 2, None) == glop.EINVAL
+    assert lib.glop_ingest_create(p, 1 << 20, 0, 0, ctypes.byref(h)) == glop.EINVAL
+    assert lib.glop_ingest_create(p, 1 << 20, 0, 9, ctypes.byref(h)) == glop.EINVAL
+    assert lib.glop_ingest_create(p, 0, 0, 2, ctypes.byref(h)) == glop.EINVAL
+    res = glop.IngestResult()
+    n = ctypes.c_uint32()
+    assert lib.glop_ingest_feed(None, None, 0, ctypes.byref(res)) == glop.EINVAL
+    assert lib.glop_ingest_flush(None, None, 0, ctypes.byref(n)) == glop.EINVAL
+    assert lib.glop_ingest_reset(None) == glop.EINVAL
+    assert lib.glop_ingest_info(None, None, None) == glop.EINVAL
+    assert lib.glop_ingest_destroy(None) == glop.EINVAL
