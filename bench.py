@@ -322,9 +322,22 @@ def cpu_baseline(w, budget_s: float = 20.0):
         spent += times[-1]
         if spent > budget_s:
             break
-    return {"value": round(8.0 * n / min(times) / 1e9, 4), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
-            "sample": "first %d MiB of the workload, best of %d runs (median %.4f Gbit/s), multi-threaded "
-                      "Aho-Corasick oracle" % (n >> 20, len(times), 8.0 * n / statistics.median(times) / 1e9)}
+    out = {"value": round(8.0 * n / min(times) / 1e9, 4), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+           "sample": "first %d MiB of the workload, best of %d runs (median %.4f Gbit/s), multi-threaded "
+                     "Aho-Corasick oracle" % (n >> 20, len(times), 8.0 * n / statistics.median(times) / 1e9)}
+    # the same oracle on one thread, over a smaller sample
+    n1 = min(w.nbytes, 8 << 20)
+    t0 = time.perf_counter()
+    oracle.ac(w.text[:n1], pats)
+    out["single_thread"] = {"value": round(8.0 * n1 / (time.perf_counter() - t0) / 1e9, 4), "unit": "Gbit/s",
+                            "sample": "first %d MiB, one run, Aho-Corasick oracle on one thread" % (n1 >> 20)}
+    # the naive every-pattern-at-every-offset oracle, on the small configuration only
+    if w.nbytes <= (1 << 20):
+        t0 = time.perf_counter()
+        oracle.naive(w.text, pats)
+        out["naive"] = {"value": round(8.0 * w.nbytes / (time.perf_counter() - t0) / 1e9, 4), "unit": "Gbit/s",
+                        "sample": "the whole %d-byte text, one run, one thread" % w.nbytes}
+    return out
 
 
 def run_prefix_fp(args, ws, rank):
@@ -561,6 +574,8 @@ def main():
 
     w = make_workload(args.workload)
     N = w.nbytes
+    import hashlib
+    text_sha = hashlib.sha256(memoryview(np.ascontiguousarray(w.text))).hexdigest()  # logged with the line
     host = torch.empty(N, dtype=torch.uint8, pin_memory=True)
     host.numpy()[:] = w.text
     text = host.to(dev)
@@ -738,7 +753,8 @@ def main():
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_max / args.steps, 5), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": args.workload, "text_bytes": N, "patterns": w.patterns.n, "matches": M,
+        "config": {"workload": args.workload, "text_bytes": N, "text_sha256": text_sha, "patterns": w.patterns.n,
+                   "matches": M,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "dp%d (independent shards)" % ws},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,
