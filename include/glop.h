@@ -255,9 +255,9 @@ glop_status glop_scan_host(glop_handle h, const uint8_t *h_text, uint64_t len, g
  * into (the paper's overlap of the next batch's transfer with the current
  * scan, Sec. 6): piece k is bytes [bounds[k], bounds[k + 1]) for
  * k < *n_pieces, with bounds[0] = 0, bounds[*n_pieces] = len, strictly
- * increasing, inner bounds multiples of 4096.  Texts under 64 MiB go in one
+ * increasing, inner bounds multiples of 4096.  Texts under 16 MiB go in one
  * piece; longer ones in at most 9: a short first piece, then equal full
- * pieces (8 at most, and at most one per 32 MiB of text).
+ * pieces (8 at most, and at most one per 8 MiB of text).
  * (glop_scan_host scans an automaton without patterns in one piece whatever
  * the length.)  Each piece's scan also reads the next longest-pattern - 1
  * bytes; its upload is issued with them.  Host only, no device work.

@@ -290,7 +290,7 @@ namespace {
 // one (the copy-back of the first matches starts after a short upload and scan), then up to kMidPieces equal
 // full pieces, at most one per kPieceMin bytes.  kTailDiv > 0 would end on a short piece as well; on GB300 that
 // measured no faster (the copy-back, not the last scan, ends the call).
-constexpr uint64_t kPieceMin = 32ull << 20;
+constexpr uint64_t kPieceMin = 8ull << 20;
 constexpr uint32_t kMidPieces = 8;
 constexpr uint32_t kHeadDiv = 4, kTailDiv = 0;  // 0: no short piece at that end
 constexpr uint32_t kMaxPieces = kMidPieces + 2;

@@ -15,12 +15,12 @@ def _lib():
     _build.build_lib()
 
 
-@pytest.mark.parametrize("n", [0, 1, 4095, 64 * MiB - 1])
+@pytest.mark.parametrize("n", [0, 1, 4095, 16 * MiB - 1])
 def test_short_texts_go_in_one_piece(n):
     assert glop.host_plan(n) == [0, n]
 
 
-@pytest.mark.parametrize("n", [64 * MiB, 64 * MiB + 1, 100 * MiB + 17, 200 * MiB + 4095, 256 * MiB, (1 << 30) + 5,
+@pytest.mark.parametrize("n", [16 * MiB, 16 * MiB + 1, 20 * MiB + 3, 64 * MiB, 100 * MiB + 17, 256 * MiB, (1 << 30) + 5,
                                (1 << 32) - 1])
 def test_long_texts_tile_in_aligned_pieces(n):
     b = glop.host_plan(n)
@@ -30,7 +30,7 @@ def test_long_texts_tile_in_aligned_pieces(n):
     assert all(x % 4096 == 0 for x in b[1:-1])
     assert 3 <= len(sizes) <= 9
     full = sizes[1:]
-    assert len(full) <= min(8, n // (32 * MiB))
+    assert len(full) <= min(8, n // (8 * MiB))
     assert len(set(full[:-1])) == 1 and full[-1] <= full[0]  # equal, the last one takes what is left
     assert full[-1] > full[0] // 2
     assert full[0] // 5 <= sizes[0] < full[0]
