@@ -46,3 +46,19 @@ def test_owned_end_rules():
     assert owned_end(0, 100, 10, False) == 90
     assert owned_end(95, 100, 10, False) == 95  # a chunk shorter than the halo owns nothing yet
     assert owned_end(95, 100, 10, True) == 100  # the last scan owns everything
+
+
+def test_native_results_become_views_of_the_rows():
+    # glop_ingest hands out (base, pointer to count (offset, pattern_id) rows, count); the wrapper views the rows
+    # in place and absolute() adds the base in uint64
+    from paper_1704_02278_gb300 import IngestResult
+    from paper_1704_02278_gb300.stream import StreamScanner
+    rows = np.array([[0, 3], [5, 1], [4294967295, 7]], dtype=np.uint32)
+    r = IngestResult(base=(1 << 33) + 11, matches=rows.ctypes.data, count=3)
+    res = StreamScanner._result(r)
+    assert res.base == (1 << 33) + 11 and len(res) == 3
+    assert np.shares_memory(res.matches, rows)
+    assert np.array_equal(res.matches, rows)
+    assert res.absolute().tolist() == [[(1 << 33) + 11, 3], [(1 << 33) + 16, 1], [(1 << 33) + 11 + 4294967295, 7]]
+    empty = StreamScanner._result(IngestResult(base=5, matches=None, count=0))
+    assert len(empty) == 0 and empty.absolute().shape == (0, 2)
