@@ -298,8 +298,12 @@ def run_reference(args, ws, rank):
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "sample_bytes": int(sample.size)},
         "cpu_baseline": {"value": round(gbps, 4), "unit": "Gbit/s", "cores": cores, "kind": "oracle",
-                         "sample": "first %.2f MiB of the workload per step (sized so all %d steps take about "
-                                   "two minutes), multi-threaded Aho-Corasick oracle" % (sample.size / 2**20, args.steps)},
+                         "sample": "first %.2f MiB of the workload per step (%s), multi-threaded Aho-Corasick "
+                                   "oracle" % (sample.size / 2**20,
+                                               "sized so all %d steps take about two minutes" % args.steps
+                                               if sample.size < min(w.nbytes, args.ref_sample_mib << 20) else
+                                               "the %d MiB cap per step" % (min(w.nbytes, args.ref_sample_mib << 20)
+                                                                            >> 20))},
         "e2e": {"value": round(gbps, 4), "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
