@@ -128,6 +128,13 @@ glop_status glop_scan_workspace_size(glop_handle h, uint64_t text_len, uint64_t 
  * glop_scan -- every (offset, pattern_id) match in d_text[0, len), sorted by
  * (offset, pattern_id), written to d_matches[0, min(count, capacity)).
  *
+ * This is the searching phase of Sec. 5: the failureless trie is walked from
+ * every byte offset (one walk per offset, a missing transition ends it), and
+ * every pattern that ends on the walk is reported at the walk's start -- the
+ * count and locations of the suspect events of the use case in Sec. 1.  With
+ * prefix_len = 0 the second stage of Sec. 2 and Sec. 5 (completing a prefix
+ * hit into a full match) is done in the same walk, so results are exact.
+ *
  * d_text       device, len bytes; any alignment (16-byte aligned is fastest).
  * len          at most 2^32 - 1 (offsets are 32-bit).  0 is valid.
  * d_matches    device, capacity entries (may be NULL when capacity is 0).
@@ -151,7 +158,9 @@ glop_status glop_batch_workspace_size(glop_handle h, uint64_t text_len, uint32_t
 
 /*
  * glop_scan_batch -- the definition of glop_scan applied to every segment of
- * one buffer (log files, packet payloads): segment s is
+ * one buffer (log files, packet payloads) -- the batches of logs that the
+ * paper's library hands to the GPU (Sec. 6), each searched as in Sec. 5:
+ * segment s is
  * d_text[d_seg_offsets[s], d_seg_offsets[s+1]); matches never cross a segment
  * end; offsets are relative to the segment start; output sorted by
  * (segment, offset, pattern_id).  One persistent launch covers all segments.
@@ -171,8 +180,14 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
  * glop_scan_status -- wait for stream, then report the outcome of the last
  * scan that used d_workspace: GLOP_OK, GLOP_EOVERFLOW (more matches than
  * capacity), GLOP_ETIMEOUT (a bounded in-kernel wait ran out), GLOP_EINVAL
- * (malformed batch offsets) or GLOP_ECUDA.  If count is not NULL it receives
- * the total match count.
+ * (malformed batch offsets), GLOP_EINTERNAL or GLOP_ECUDA.  If count is not
+ * NULL it receives the total match count -- the number of suspect events of
+ * Sec. 1; the status codes themselves have no counterpart in the paper.
+ *
+ * d_workspace NULL means the scratch array of glop_scan_noalloc on the
+ * current device: the outcome of the last glop_scan_noalloc call there
+ * (GLOP_OK before any such call).  GLOP_ECUDA when that array cannot be
+ * reached.
  */
 glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count);
 
@@ -315,17 +330,24 @@ glop_status glop_plan_destroy(glop_plan plan);
  * paper has no counterpart for this entry point.
  *
  * Arguments and results are those of glop_scan, without the workspace: the
- * scratch memory is a 25 MiB device array that the library reserves on every
- * device that loads it (held until the process exits).  len must be at most
- * 16 MiB (16777216); longer texts return GLOP_EINVAL before anything is
- * queued.  The call allocates nothing.
+ * scratch memory is a 25 MiB device array in the library.  len must be at
+ * most 16 MiB (16777216); longer texts return GLOP_EINVAL before anything is
+ * queued.  The call allocates nothing.  Conditions found on the GPU (a
+ * bounded wait that ran out, an internal check) are read with
+ * glop_scan_status(NULL, stream, &count), which reports the last
+ * glop_scan_noalloc call on the current device; an overflow also shows as
+ * *d_count > capacity.
  *
- * The first call on a device looks up the array's device address (with that
- * device current), so make that first call before any stream capture.  Every
- * call uses the same array and leaves its contents behind: two calls whose
- * work overlaps on the GPU (different streams, or different host threads)
- * race on it and give wrong results.  Serialise them, e.g. on one stream.
- * Per-call state in the array is reset by the call itself.
+ * The first call on a device (and the first after a cudaDeviceReset) loads
+ * the library's device module there, which reserves the 25 MiB, and looks up
+ * the array's device address with that device current: make that first call
+ * at start-up, before another allocator takes the device's memory and before
+ * any stream capture.  The array stays reserved on that device until the
+ * process exits.  Every call uses the same array and leaves its contents
+ * behind: two calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it and give wrong results.  Serialise
+ * them, e.g. on one stream.  Per-call state in the array is reset by the
+ * call itself.
  */
 glop_status glop_scan_noalloc(glop_handle h, const uint8_t *d_text, uint64_t len, glop_match *d_matches,
                               uint64_t capacity, uint64_t *d_count, glop_stream_t stream);
@@ -372,8 +394,9 @@ glop_status glop_scan_count(glop_handle h, const uint8_t *d_text, uint64_t len, 
 glop_status glop_batch_split(const glop_batch_match *d_matches, const uint64_t *d_count, uint64_t capacity,
                              uint32_t n_segments, glop_match *d_pairs, uint64_t *d_seg_first, glop_stream_t stream);
 
-/* glop_destroy -- free the automaton's device memory.  No scan using h may
- * still be in flight.  NULL is accepted. */
+/* glop_destroy -- free the device memory of the automaton that
+ * glop_compile built (the goto graph of Sec. 4 without failure transitions,
+ * Sec. 5).  No scan using h may still be in flight.  NULL is accepted. */
 glop_status glop_destroy(glop_handle h);
 
 /* Static description of a status code. */

@@ -254,7 +254,9 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
 }
 
 glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count) {
-    if (!d_workspace) return GLOP_EINVAL;
+    // NULL: the scratch array of glop_scan_noalloc on the current device
+    if (!d_workspace) d_workspace = glop::noalloc_scratch_of_current_device();
+    if (!d_workspace) return GLOP_ECUDA;
     uint32_t hdr[16];
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(st) != cudaSuccess) return GLOP_ECUDA;

@@ -28,35 +28,73 @@ static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes]
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
+struct Cached {
+    unsigned long long ctx_id = 0;  // the CUDA context the address belongs to (0 = none yet)
+    void *ptr = nullptr;
+};
+Cached g_scratch[kMaxDevices];
 
-// The device address of the array on the current device, looked up once per
-// device (the host-side symbol is only a stand-in and must never be passed to
-// a kernel).  nullptr when the lookup fails.
-void *scratch_of_current_device() {
+// The process-unique id of the calling thread's current CUDA context, or 0
+// when there is none (or the driver cannot tell).  Read through the driver's
+// cuCtxGetId, reached by the runtime's entry-point query so that the library
+// does not link the driver library itself.
+unsigned long long current_context_id() {
+    using CtxGetId = int (*)(void *, unsigned long long *);
+    static const CtxGetId fn = []() -> CtxGetId {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<CtxGetId>(f);
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != 0) return 0;
+    return id;
+}
+
+}  // namespace
+
+namespace glop {
+
+// The device address of the array in the current device's context, with that
+// device current.  The host-side symbol is only a stand-in and must never be
+// passed to a kernel.  The address is looked up once per device and context:
+// the first call on a device loads the module and reserves the array; after
+// a cudaDeviceReset the next call finds a new context and looks it up again.
+// nullptr when the lookup fails.
+void *noalloc_scratch_of_current_device() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    Cached &c = g_scratch[dev];
+    const unsigned long long id = current_context_id();
+    if (!c.ptr || !id || id != c.ctx_id) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
-        g_scratch_ptr[dev] = p;
+        c.ptr = p;
+        c.ctx_id = current_context_id();  // the lookup made the device's context current if it was not
     }
-    return g_scratch_ptr[dev];
+    return c.ptr;
 }
 
-}  // namespace
+}  // namespace glop
+
 
 extern "C" glop_status glop_scan_noalloc(glop_handle h, const uint8_t *d_text, uint64_t len, glop_match *d_matches,
                                          uint64_t capacity, uint64_t *d_count, glop_stream_t stream) {
     if (len > kNoAllocMaxLen) return GLOP_EINVAL;
     if (glop::workspace_bytes(len, false) > kNoAllocScratchBytes) return GLOP_EINVAL;
-    void *ws = scratch_of_current_device();
+    void *ws = glop::noalloc_scratch_of_current_device();
     if (!ws) return GLOP_ECUDA;
-    // The header of the scratch is cleared by the scan itself on the stream
-    // before any kernel reads it; everything else is written before it is read.
+    // The header of the scratch (status flags, ticket, total, barrier counters)
+    // is cleared by the scan itself on the stream before any kernel reads it;
+    // everything else is written before it is read.  The header then holds this
+    // call's outcome until the next call: glop_scan_status(NULL, ...) reads it.
     return glop_scan(h, d_text, len, d_matches, capacity, d_count, ws, kNoAllocScratchBytes, stream);
 }

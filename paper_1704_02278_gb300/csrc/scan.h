@@ -51,6 +51,8 @@ uint64_t workspace_bytes(uint64_t len, bool batch);
 uint64_t count_workspace_bytes(uint32_t n_states);
 // returns a glop_status value
 int launch_scan(const ScanLaunch &L);
+// The scratch array of glop_scan_noalloc on the current device (its workspace), or nullptr.
+void *noalloc_scratch_of_current_device();
 // Queue a one-thread kernel writing the scan's count and status (as glop_scan_words) to h_words_dev, a
 // device-side address of pinned host memory.  Returns a glop_status value.
 int launch_words(const void *d_workspace, unsigned long long *h_words_dev, cudaStream_t stream);

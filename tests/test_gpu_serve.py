@@ -1,7 +1,11 @@
-"""Serving: every request's result is the same alone and in the continuous-batching mix."""
+"""Serving: every request's result is the same alone and in the continuous-batching mix, and each
+equals the CPU oracle's match list for its payload and pattern set."""
+import hashlib
+
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -25,16 +29,34 @@ def _requests(n=80, max_size=2 << 20, span=0.4):
     return reqs
 
 
+_ORACLE_CACHE = {}
+
+
+def _oracle(sets, r):
+    """The oracle's (offset, pattern_id) list for one request (cached by the contents of its pattern set
+    and payload)."""
+    pats = sets[r.set_index]
+    text = r.payload.numpy()
+    key = (hashlib.sha1(pats.buf.tobytes() + pats.offs.tobytes()).hexdigest(), hashlib.sha1(text).hexdigest())
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = oracle.ac_mt(text, pats.csr())
+    return _ORACLE_CACHE[key]
+
+
 def _solo(sets, reqs):
+    """Each request scanned alone on the GPU; every solo result must equal the oracle's before it is
+    used as the expected value of a served run."""
     autos = {}
     out = []
     for r in reqs:
         a = autos.setdefault(r.set_index, glop.Automaton(sets[r.set_index]))
         if r.payload.numel() == 0:
             out.append(np.zeros((0, 2), np.uint32))
-            continue
-        m, n = a.scan(r.payload.cuda())
-        out.append(m.cpu().numpy().view(np.uint32))
+        else:
+            m, n = a.scan(r.payload.cuda())
+            out.append(m.cpu().numpy().view(np.uint32))
+        ref = _oracle(sets, r)
+        assert np.array_equal(out[-1].reshape(-1, 2), ref), ("solo scan != oracle", r.rid)
     return out
 
 
@@ -109,3 +131,43 @@ def test_empty_and_tiny_requests():
         for r, e in zip(reqs, exp):
             assert r.count == len(e), (realtime, r.rid)
             assert np.array_equal(r.matches.reshape(-1, 2), e.reshape(-1, 2)), (realtime, r.rid)
+
+
+def test_config5_trace_sample_vs_oracle():
+    """The first 200 requests of the 60 s, 200 req/s serving trace (all 8 resident sets, the 20,000-pattern
+    set included; syslog and packet payloads; trace sizes up to 16 MiB), served by continuous batching at the
+    trace's own arrival times and then saturated: every request's match list equals the oracle's."""
+    sets = W.config5_sets()
+    times, sizes, set_idx = W.config5_requests(200.0, 60.0)
+    n = 200
+    pool = 32 << 20
+    pools = [torch.from_numpy(W.config5_payload(k, pool)).pin_memory() for k in (0, 1)]
+    reqs = []
+    for i in range(n):
+        size = int(min(sizes[i], 16 << 20))
+        off = (i * 2654435761) % (pool - size + 1)
+        reqs.append(serve.Request(i, int(set_idx[i]), pools[i % 2][off:off + size], float(times[i])))
+    assert {r.set_index for r in reqs} == set(range(8))
+    assert any(r.set_index == 7 and r.rid % 2 == 1 for r in reqs)  # 20k set on packet payloads
+    assert any(r.set_index == 7 and r.rid % 2 == 0 for r in reqs)  # 20k set on syslog payloads
+    # the oracle once per set, over that set's requests as segments of one buffer
+    exp = {}
+    for si in range(8):
+        rs = [r for r in reqs if r.set_index == si]
+        seg = np.zeros(len(rs) + 1, np.uint64)
+        seg[1:] = np.cumsum([r.payload.numel() for r in rs])
+        buf = np.concatenate([r.payload.numpy() for r in rs])
+        res = oracle.batch(buf, seg, sets[si].csr())
+        cut = np.searchsorted(res[:, 0], np.arange(len(rs) + 1), side="left")
+        for k, r in enumerate(rs):
+            exp[r.rid] = np.ascontiguousarray(res[cut[k]:cut[k + 1], 1:])
+    srv = serve.BatchServer(sets, hbm_budget=2 << 30, keep_matches=True)
+    for realtime in (True, False):
+        for r in reqs:
+            r.count, r.matches, r.done = -1, None, -1.0
+        wall, st = srv.serve(reqs, realtime=realtime)
+        assert st["batches"] >= 1
+        for r in reqs:
+            e = exp[r.rid]
+            assert r.count == len(e), (realtime, r.rid, r.set_index)
+            assert np.array_equal(r.matches.reshape(-1, 2), e), (realtime, r.rid, r.set_index)
