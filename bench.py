@@ -190,6 +190,33 @@ def walk_stats(w, sample_bytes: int = 8 << 20):
             "source": "host walk emulation (same decision rules), sample of the workload"}
 
 
+def verify_output(w, matches, M: int, sample_bytes: int = 64 << 20):
+    """Compare the scan output left in ``matches`` by the timed steps with the oracle.  Single buffer: the
+    whole (offset, pattern_id) list against the multi-threaded Aho-Corasick oracle.  Batches: every segment
+    that starts in the first ``sample_bytes`` of the buffer, against the oracle's per-segment scan of those
+    segments (the oracle is too slow for all of config 3 or 4 within the bench's minutes)."""
+    import oracle
+    import torch
+    t0 = time.perf_counter()
+    if w.seg is None:
+        got = matches[:M].cpu().numpy().view(np.uint32)
+        exp = oracle.ac_mt(w.text, w.patterns.csr())
+        ok = bool(len(exp) == M and np.array_equal(got, exp))
+        what = "all %d matches vs oracle.ac_mt on the whole text" % M
+    else:
+        k = int(np.searchsorted(w.seg, sample_bytes, side="right"))
+        k = max(1, min(k, len(w.seg) - 1))
+        seg = np.ascontiguousarray(w.seg[:k + 1], dtype=np.uint64)
+        exp = oracle.batch(w.text[:int(seg[-1])], seg, w.patterns.csr())
+        col = matches[:M, 0].contiguous()
+        n = int(torch.searchsorted(col, torch.tensor([k], dtype=col.dtype, device=col.device)).item())
+        del col
+        got = matches[:n].cpu().numpy().view(np.uint32)
+        ok = bool(n == len(exp) and np.array_equal(got, exp))
+        what = "segments 0..%d (%d bytes, %d matches) vs oracle.batch" % (k - 1, int(seg[-1]), len(exp))
+    return {"ok": ok, "checked": what, "seconds": round(time.perf_counter() - t0, 2)}
+
+
 def make_workload(name: str):
     import workloads as W
     if name == "syslog-256MiB-1000pat":
@@ -476,20 +503,14 @@ def run_stream(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args, ws, rank):
-    """Serving trace (Poisson arrivals, log-normal sizes, 8 resident sets): plain per-request scans vs
-    continuous batching, in real time (latency) and saturated (throughput)."""
-    if rank != 0:
-        return
+def serve_record(seconds: float, hbm_gib: int, saturated_runs: int = 3):
+    """Serving trace (Poisson arrivals at 200 req/s, log-normal sizes, 8 resident sets): plain per-request
+    scans vs continuous batching, in real time (latency) and saturated (throughput).  Returns the record."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     import workloads as W
     from paper_1704_02278_gb300 import serve
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     sets = W.config5_sets()
-    times, sizes, set_idx = W.config5_requests(200.0, float(args.serve_seconds))
+    times, sizes, set_idx = W.config5_requests(200.0, float(seconds))
     pool_bytes = 256 << 20
     pools = [torch.from_numpy(W.config5_payload(k, pool_bytes)).pin_memory() for k in (0, 1)]
 
@@ -501,10 +522,10 @@ def run_serve(args, ws, rank):
             reqs.append(serve.Request(i, int(set_idx[i]), pools[i % 2][off:off + size], float(times[i])))
         return reqs
 
-    out = {"requests": len(times), "bytes": int(sizes.sum()), "seconds": args.serve_seconds}
+    out = {"requests": len(times), "bytes": int(sizes.sum()), "seconds": seconds}
     plain = serve.PlainServer(sets, max_request_bytes=int(sizes.max()))
     # pinned result buffers sized for a full 256 MiB batch at up to 0.25 matches per byte
-    batched = serve.BatchServer(sets, hbm_budget=args.serve_hbm_gib << 30, out_rows=(256 << 20) // 4)
+    batched = serve.BatchServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4)
     # warm both (first launches, host allocator)
     plain.serve(make()[:20], realtime=False)
     batched.serve(make()[:20], realtime=False)
@@ -512,23 +533,96 @@ def run_serve(args, ws, rank):
         reqs = make()
         wall, st = srv.serve(reqs, realtime=True)
         lat = serve.latency_summary(reqs)
-        # saturation: every request available at once; three runs (the host loop is sensitive to the
+        # saturation: every request available at once; several runs (the host loop is sensitive to the
         # shared host's load), median reported, best kept beside it
         walls = []
-        for _ in range(3):
+        for _ in range(saturated_runs):
             reqs2 = make()
             wall2, st2 = srv.serve(reqs2, realtime=False)
             walls.append(wall2)
         wmed = statistics.median(walls)
         out[name] = dict(lat, realtime_wall_s=round(wall, 3), realtime_stats=st, saturated_s=round(wmed, 3),
                          saturated_gbps=round(8.0 * out["bytes"] / wmed / 1e9, 3),
-                         saturated_gbps_best=round(8.0 * out["bytes"] / min(walls) / 1e9, 3), stats=st2,
-                         matches=int(sum(r.count for r in reqs2)))
+                         saturated_gbps_best=round(8.0 * out["bytes"] / min(walls) / 1e9, 3),
+                         saturated_runs=len(walls), stats=st2, matches=int(sum(r.count for r in reqs2)))
+    del plain, batched, pools
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serve(args, ws, rank):
+    """The serving trace alone (config 5), for --serve-seconds of arrivals."""
+    if rank != 0:
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    out = serve_record(args.serve_seconds, args.serve_hbm_gib)
     line = {"metric": "served p50/p99 latency (ms) and saturated Gbit/s: continuous batching vs plain",
             "value": out["batched"]["saturated_gbps"], "unit": "Gbit/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": "serve-200rps-%ds-8sets" % args.serve_seconds}, "serve": out}
     print(json.dumps(line), flush=True)
+
+
+def dpi_record(dev, steps: int, warmup: int, local: int):
+    """The 20,000-signature point (config 3): 2 GiB of packets scanned as one batch, each step one replay of
+    the captured scan (a single CUDA-graph launch), device-resident input, CUDA events on the launching
+    stream; the timed output is checked against the oracle on a sample of whole packets."""
+    import torch
+    import paper_1704_02278_gb300 as glop
+    w = make_workload("dpi-2GiB-20000sig")
+    N = w.nbytes
+    text = torch.from_numpy(w.text).to(dev)
+    seg = torch.from_numpy(w.seg.view(np.int64).copy()).to(dev)
+    a = glop.Automaton(w.patterns)
+    stream = torch.cuda.Stream(device=dev)
+    m0, M = a.scan_batch(text, seg, stream=stream)
+    del m0
+    torch.cuda.empty_cache()
+    matches = torch.empty((max(M, 1), 3), dtype=torch.int32, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    plan = glop.Plan(a, text, matches, count, seg_offsets=seg, stream=stream)
+    clocks = ClockSampler(local).start()
+    for _ in range(warmup):
+        plan.launch(stream)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        e0.record(stream)
+        plan.launch(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per = [e0.elapsed_time(e1) for e0, e1 in ev]
+    st = a.status(dev, stream=stream, batch=True)
+    assert st == glop.OK, "scan status %s" % glop.STATUS.get(st)
+    assert int(count.item()) == M
+    verified = verify_output(w, matches, M)
+    ms = statistics.mean(per)
+    hbm, which = peaks()
+    halo = a.info["max_pattern_len"]
+    n_chunks = (N + CHUNK - 1) // CHUNK
+    n_tiles = (N + SUBTILE - 1) // SUBTILE
+    algo_bytes = N + n_chunks * min(max(halo - 1, 16), 1024) + 12 * M + 16 * n_tiles
+    achieved = algo_bytes / (ms / 1e3) / 1e9
+    rec = {"workload": "dpi-2GiB-20000sig", "text_bytes": N, "segments": int(len(w.seg) - 1),
+           "patterns": w.patterns.n, "matches": M, "steps": steps, "warmup": warmup,
+           "ms_per_step": round(ms, 4), "median_ms": round(statistics.median(per), 4),
+           "value": round(8.0 * N / (ms / 1e3) / 1e9, 3), "unit": "Gbit/s",
+           "launch": "cuda graph (memset + init + scan kernel) per step", "gpu_launches": 2 * steps,
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(achieved / hbm, 4), "traffic": profiled_traffic("dpi-2GiB-20000sig"),
+                        "note": "algorithmic bytes = text + halo re-reads + 12 B/match + tile status; peak %s"
+                                % which},
+           "hbm_input_frac": round(N / (ms / 1e3) / 1e9 / hbm, 4),
+           "verified": verified["ok"], "verification": verified, "clocks": clk}
+    del plan, matches, text, seg, count
+    a.close()
+    torch.cuda.empty_cache()
+    return rec
 
 
 def main():
@@ -545,6 +639,9 @@ def main():
                     help="skip the read-stream peak, walk statistics and count-only timing")
     ap.add_argument("--per-segment-steps", type=int, default=1)
     ap.add_argument("--serve-seconds", type=int, default=60)
+    ap.add_argument("--extra-serve-seconds", type=int, default=20,
+                    help="arrival seconds of the serving trace replayed for the default line's serve record")
+    ap.add_argument("--dpi-steps", type=int, default=50)
     ap.add_argument("--serve-hbm-gib", type=int, default=16)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -637,6 +734,9 @@ def main():
     st = a.status(dev, stream=stream, batch=seg is not None)
     assert st == glop.OK, "scan status %s" % glop.STATUS.get(st)
     assert int(count.item()) == M
+    # the match list the timed steps wrote, compared element by element with the CPU oracle (outside the
+    # timed region): the whole list for a single buffer; for batches a sample of whole segments
+    verified = verify_output(w, matches, M)
 
     t_max = total_ms
     if pg:
@@ -767,6 +867,7 @@ def main():
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
         "launch": "cuda graph (memset + init + scan kernel) per step" if plan is not None else "glop_scan per step",
+        "verified": verified["ok"], "verification": verified,
         "hbm_input_frac": round(N / (avg_launch_ms / 1e3) / 1e9 / hbm, 4),
         "step_ms": {"mean": round(statistics.mean(per), 5), "median": round(statistics.median(per), 5),
                     "p10": round(float(np.percentile(per, 10)), 5), "p90": round(float(np.percentile(per, 90)), 5),
@@ -801,6 +902,16 @@ def main():
         line["per_segment_launches"] = per_segment
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
+    # the metric's other halves on the same box and run: the 20k-signature point and serving
+    if args.workload == "syslog-256MiB-1000pat" and not args.no_extras and ws == 1:
+        del text, matches, ws_buf, host
+        torch.cuda.empty_cache()
+        line["dpi_20k"] = dpi_record(dev, args.dpi_steps, args.warmup if args.warmup < 10 else 5, local)
+        if args.extra_serve_seconds > 0:
+            sv = serve_record(args.extra_serve_seconds, args.serve_hbm_gib, saturated_runs=3)
+            sv["note"] = ("the config-5 trace's first %d s of arrivals (200 req/s; the full trace is 60 s: "
+                          "bench.py --workload serve)" % args.extra_serve_seconds)
+            line["serve"] = sv
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
