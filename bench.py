@@ -525,7 +525,9 @@ def serve_record(seconds: float, hbm_gib: int, saturated_runs: int = 3):
     out = {"requests": len(times), "bytes": int(sizes.sum()), "seconds": seconds}
     plain = serve.PlainServer(sets, max_request_bytes=int(sizes.max()))
     # pinned result buffers sized for a full 256 MiB batch at up to 0.25 matches per byte
-    batched = serve.BatchServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4)
+    # requests of 8 MiB and more go to the large-request lane, sized like the plain server's buffers
+    batched = serve.BatchServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4,
+                                max_request_bytes=int(sizes.max()))
     # warm both (first launches, host allocator)
     plain.serve(make()[:20], realtime=False)
     batched.serve(make()[:20], realtime=False)
@@ -545,6 +547,7 @@ def serve_record(seconds: float, hbm_gib: int, saturated_runs: int = 3):
                          saturated_gbps=round(8.0 * out["bytes"] / wmed / 1e9, 3),
                          saturated_gbps_best=round(8.0 * out["bytes"] / min(walls) / 1e9, 3),
                          saturated_runs=len(walls), stats=st2, matches=int(sum(r.count for r in reqs2)))
+    batched.close()
     del plain, batched, pools
     torch.cuda.empty_cache()
     return out

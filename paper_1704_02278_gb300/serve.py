@@ -13,6 +13,11 @@ layer: several compiled pattern sets stay resident on the device, requests
   ``glop_scan_batch`` launch (one segment per request) while earlier batches
   are still on the GPU -- up to ``max_inflight`` batches overlap, each on its
   own stream, so copies of one batch run under the scan of another,
+* sends a request of at least ``big_bytes`` to a lane of its own: a worker
+  thread that scans it end to end through ``glop_scan_host`` (uploads, scans
+  and copy-backs of its pieces overlapped) into a pinned result buffer sized
+  up front, so a large request neither waits for a batch nor holds the
+  batches of small requests behind it,
 * returns each request's matches as (offset, pattern_id) pairs and its
   latency from arrival to results on the host.
 
@@ -113,6 +118,77 @@ class _Batch:
     pass
 
 
+class _BigLane:
+    """One worker thread serving large requests in arrival order through the end-to-end glop_scan_host call
+    (pieces uploaded, scanned and copied back overlapped) on its own stream, staging and pinned result rows.
+    The library call releases the interpreter lock, so the serving loop keeps batching meanwhile."""
+
+    def __init__(self, torch, device, automata, max_bytes: int, out_rows: int, keep: bool):
+        import queue
+        import threading
+        self.torch, self.device, self.automata, self.keep = torch, device, automata, keep
+        self.lib = lib()
+        self.max_bytes = max_bytes
+        self.stream = torch.cuda.Stream(device=device)
+        self._size(out_rows)
+        self.q = queue.Queue()
+        self.completed = 0
+        self.rescans = 0
+        self.error = None
+        self.t0 = 0.0
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _size(self, rows: int):
+        torch = self.torch
+        need = ctypes.c_uint64()
+        self.lib.glop_scan_host_staging_size(self.automata[0].handle, self.max_bytes, rows, ctypes.byref(need))
+        self.staging = torch.empty(int(need.value), dtype=torch.uint8, device=self.device)
+        self.out = torch.empty((rows, 2), dtype=torch.int32, pin_memory=True)
+        self.rows = rows
+
+    def _run(self):
+        torch = self.torch
+        cnt = ctypes.c_uint64()
+        try:
+            dev = self.device.index if self.device.index is not None else torch.cuda.current_device()
+            torch.cuda.set_device(dev)
+        except Exception as e:  # reported by the serving loop; requests still count as finished
+            self.error = e
+        while True:
+            r = self.q.get()
+            if r is None:
+                return
+            if self.error is not None:
+                self.completed += 1
+                continue
+            try:
+                n = r.payload.numel()
+                while True:
+                    rc = self.lib.glop_scan_host(self.automata[r.set_index].handle, r.payload.data_ptr(), n,
+                                                 self.out.data_ptr(), self.rows, ctypes.byref(cnt),
+                                                 self.staging.data_ptr(), self.staging.numel(),
+                                                 self.stream.cuda_stream)
+                    if rc == EOVERFLOW:  # more matches than the rows sized up front: grow once and scan again
+                        self.rescans += 1
+                        self._size(int(cnt.value) + (1 << 20))
+                        continue
+                    if rc != OK:
+                        raise GlopError(rc, "glop_scan_host")
+                    break
+                r.count = int(cnt.value)
+                if self.keep:
+                    r.matches = self.out[:r.count].numpy().view(np.uint32).copy()
+                r.done = time.perf_counter() - self.t0
+            except Exception as e:  # reported by the serving loop
+                self.error = e
+            self.completed += 1
+
+    def close(self):
+        self.q.put(None)
+        self.thread.join()
+
+
 class BatchServer:
     """Continuous batching of scan requests over resident automata (see module doc).
 
@@ -133,7 +209,8 @@ class BatchServer:
 
     def __init__(self, pattern_sets, hbm_budget: int = 8 << 30, max_inflight: int = 4,
                  max_batch_bytes: int = 256 << 20, max_batch_requests: int = 512, keep_matches: bool = False,
-                 out_rows: int | None = None, fast_bytes: int = 1 << 20, device=None):
+                 out_rows: int | None = None, fast_bytes: int = 1 << 20, big_bytes: int = 8 << 20,
+                 max_request_bytes: int = 0, big_out_rows: int | None = None, device=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -163,6 +240,20 @@ class BatchServer:
             self.fast_staging = torch.empty(int(need.value), dtype=torch.uint8, device=self.device)
             self.fast_out = torch.empty((self.fast_cap, 2), dtype=torch.int32, pin_memory=True)
             self.fast_stream = torch.cuda.Stream(device=self.device)
+        # the lane for requests of at least big_bytes (0 = none): sized for max_request_bytes, with result rows
+        # for two matches per payload byte unless big_out_rows says otherwise
+        self.big_bytes = big_bytes if max_request_bytes >= big_bytes > 0 else 0
+        self.big = None
+        if self.big_bytes:
+            rows = big_out_rows if big_out_rows is not None else 2 * max_request_bytes
+            self.big = _BigLane(torch, self.device, self.automata, max_request_bytes, max(rows, 1 << 16),
+                                keep_matches)
+
+    def close(self):
+        """Stop the large-request worker (the server is unusable afterwards)."""
+        if self.big is not None:
+            self.big.close()
+            self.big = None
 
     # -- one batch -------------------------------------------------------------
     def _cap(self, si: int, nbytes: int) -> int:
@@ -294,8 +385,11 @@ class BatchServer:
         requests are available at once (saturation).  Returns (wall seconds, stats of this call)."""
         import collections
         torch = self.torch
-        self.stats = {"batches": 0, "rescans": 0, "requests_per_batch_max": 0, "admission_waits": 0, "fast": 0}
+        self.stats = {"batches": 0, "rescans": 0, "requests_per_batch_max": 0, "admission_waits": 0, "fast": 0,
+                      "big": 0}
         cnt = ctypes.c_uint64()
+        big = self.big
+        big_done0 = big.completed if big is not None else 0
         fifos = [collections.deque() for _ in self.automata]
         order = collections.deque()  # arrival order over all sets; requests already batched are skipped
         batched = set()
@@ -304,14 +398,23 @@ class BatchServer:
         nxt = 0
         n = len(requests)
         t0 = time.perf_counter()
+        if big is not None:
+            big.t0 = t0
         done = 0
-        while done < n:
+        n_big = 0
+        while done + ((big.completed - big_done0) if big is not None else 0) < n:
             now = time.perf_counter() - t0
             while nxt < n and (not realtime or requests[nxt].arrival <= now):
                 r = requests[nxt]
-                fifos[r.set_index].append(r)
-                order.append(r)
+                if big is not None and r.payload.numel() >= self.big_bytes:
+                    big.q.put(r)  # the large-request lane: no batch, no wait behind small ones
+                    n_big += 1
+                else:
+                    fifos[r.set_index].append(r)
+                    order.append(r)
                 nxt += 1
+            if big is not None and (big.error is not None or not big.thread.is_alive()):
+                raise big.error or RuntimeError("the large-request lane stopped")
             progressed = False
             # completions
             for b in list(inflight):
@@ -379,7 +482,12 @@ class BatchServer:
             if not progressed:
                 if realtime and not inflight and not order and nxt < n:
                     time.sleep(max(0.0, min(requests[nxt].arrival - (time.perf_counter() - t0), 0.0005)))
+                elif big is not None and (inflight or n_big):
+                    time.sleep(0)  # let the lane's thread take the interpreter lock between its library calls
         torch.cuda.synchronize(self.device)
+        self.stats["big"] = n_big
+        if big is not None:
+            self.stats["big_rescans"] = big.rescans
         return time.perf_counter() - t0, dict(self.stats)
 
 

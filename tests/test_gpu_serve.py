@@ -161,13 +161,20 @@ def test_config5_trace_sample_vs_oracle():
         cut = np.searchsorted(res[:, 0], np.arange(len(rs) + 1), side="left")
         for k, r in enumerate(rs):
             exp[r.rid] = np.ascontiguousarray(res[cut[k]:cut[k + 1], 1:])
-    srv = serve.BatchServer(sets, hbm_budget=2 << 30, keep_matches=True)
+    # requests of 4 MiB and more take the large-request lane (end-to-end scans in a worker thread); its result
+    # rows are sized far too small at first, so it also grows them and scans again
+    srv = serve.BatchServer(sets, hbm_budget=2 << 30, keep_matches=True, big_bytes=4 << 20,
+                            max_request_bytes=16 << 20, big_out_rows=1 << 16)
+    assert sum(r.payload.numel() >= (4 << 20) for r in reqs) >= 3
     for realtime in (True, False):
         for r in reqs:
             r.count, r.matches, r.done = -1, None, -1.0
         wall, st = srv.serve(reqs, realtime=realtime)
-        assert st["batches"] >= 1
+        assert st["batches"] >= 1 and st["big"] >= 3
+        assert all(r.done >= r.arrival or not realtime for r in reqs)
         for r in reqs:
             e = exp[r.rid]
             assert r.count == len(e), (realtime, r.rid, r.set_index)
             assert np.array_equal(r.matches.reshape(-1, 2), e), (realtime, r.rid, r.set_index)
+    assert srv.big.rescans >= 1
+    srv.close()
