@@ -77,6 +77,12 @@ typedef struct {
     /* Start filter bitmap of 2^filter_bits_log2 bits (13..19; 0 = the
      * library's choice from the number of distinct grams). */
     uint32_t filter_bits_log2;
+    /* Text staged per bulk copy: every consumer warp of a thread block takes
+     * chunk_subtiles consecutive 1 KiB sub-tiles (32 start offsets per lane)
+     * of each staged chunk.  0 or 1: 31 KiB chunks; 2: 62 KiB chunks (in two
+     * ring slots, when they fit in shared memory beside the tables; else 31
+     * KiB).  Other values are taken as 1. */
+    uint32_t chunk_subtiles;
 } glop_compile_opts;
 
 /* Facts about a compiled automaton (glop_info_get). */
@@ -183,6 +189,9 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
  * (malformed batch offsets), GLOP_EINTERNAL or GLOP_ECUDA.  If count is not
  * NULL it receives the total match count -- the number of suspect events of
  * Sec. 1; the status codes themselves have no counterpart in the paper.
+ * When several conditions were raised, GLOP_ETIMEOUT is reported first: after
+ * a wait ran out the rest of the scan may meet scratch data that was never
+ * written, and the checks that catch it (GLOP_EINTERNAL) are its consequence.
  *
  * d_workspace NULL means the scratch array of glop_scan_noalloc on the
  * current device: the outcome of the last glop_scan_noalloc call there
@@ -285,7 +294,9 @@ glop_status glop_scan_host_plan(uint64_t len, uint64_t *bounds, uint32_t max_bou
 /*
  * glop_tune -- pick compile options for a pattern set by timing scans of a
  * sample on the current device: the start filter's gram length and bitmap
- * size and the shared-memory budget of on-chip transition rows.  Every
+ * size, the shared-memory budget of on-chip transition rows and the text
+ * staged per bulk copy (31 or 62 KiB chunks; a 62 KiB candidate that does not
+ * fit in shared memory is not timed).  Every
  * candidate is compiled, warmed up and timed over `repeats` scans of the
  * sample (d_sample, sample_len; a batch when d_seg_offsets is not NULL) with
  * CUDA events on stream.  points[0 .. *n_points) receive every candidate and

@@ -55,7 +55,8 @@ class GlopError(RuntimeError):
 
 class glop_compile_opts(ctypes.Structure):
     _fields_ = [("prefix_len", ctypes.c_uint32), ("smem_budget_bytes", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("gram_len", ctypes.c_uint32), ("filter_bits_log2", ctypes.c_uint32)]
+                ("gram_len", ctypes.c_uint32), ("filter_bits_log2", ctypes.c_uint32),
+                ("chunk_subtiles", ctypes.c_uint32)]
 
 
 class glop_tune_point(ctypes.Structure):
@@ -180,7 +181,7 @@ class Automaton:
     """
 
     def __init__(self, patterns, prefix_len: int = 0, smem_budget: int = 0, gram_len: int = 0,
-                 filter_bits_log2: int = 0, options: dict | None = None):
+                 filter_bits_log2: int = 0, options: dict | None = None, chunk_subtiles: int = 0):
         L = lib()
         buf, offs = _pattern_csr(patterns)
         if buf.size == 0:
@@ -190,7 +191,8 @@ class Automaton:
             smem_budget = options.get("smem_budget_bytes", smem_budget)
             gram_len = options.get("gram_len", gram_len)
             filter_bits_log2 = options.get("filter_bits_log2", filter_bits_log2)
-        opts = glop_compile_opts(prefix_len, smem_budget, 0, gram_len, filter_bits_log2)
+            chunk_subtiles = options.get("chunk_subtiles", chunk_subtiles)
+        opts = glop_compile_opts(prefix_len, smem_budget, 0, gram_len, filter_bits_log2, chunk_subtiles)
         h = ctypes.c_void_p()
         _check(L.glop_compile(buf.ctypes.data, offs.ctypes.data, len(offs) - 1, ctypes.byref(opts),
                               ctypes.byref(h)), "glop_compile")

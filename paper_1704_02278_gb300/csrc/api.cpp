@@ -19,6 +19,8 @@ struct glop_automaton {
     int device = 0;
     glop_info info{};
     uint32_t smem_budget = 0;
+    uint32_t ksub = 1;  // sub-tiles per consumer warp and staged chunk (chunks of 31 or 62 KiB)
+    uint32_t ksub_used = 1;  // what the last scan launch used (62 KiB chunks fall back to 31 when they do not fit)
 };
 
 namespace {
@@ -84,7 +86,8 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
     uint64_t o_rows = al(o_cls + 256);
     uint64_t o_chain = al(o_rows + rows_bytes + 16);
     uint64_t o_cum = al(o_chain + bytes_of(H.chain) + 16);
-    uint64_t o_ids = al(o_cum + bytes_of(H.cum_off));
+    uint64_t o_outl = al(o_cum + bytes_of(H.cum_off));
+    uint64_t o_ids = al(o_outl + 8ull * H.n_states);
     uint64_t o_bm = al(o_ids + bytes_of(H.cum_ids) + 16);
     uint64_t o_gr = al(o_bm + bytes_of(H.bitmap) + 16);
     uint64_t total = al(o_gr + bytes_of(H.grams) + 16);
@@ -99,6 +102,13 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
                                 rows_bytes);
     if (!H.chain.empty()) std::memcpy(host.data() + o_chain, H.chain.data(), bytes_of(H.chain));
     std::memcpy(host.data() + o_cum, H.cum_off.data(), bytes_of(H.cum_off));
+    {
+        uint32_t *ol = reinterpret_cast<uint32_t *>(host.data() + o_outl);
+        for (uint32_t t = 0; t < H.n_states; ++t) {
+            ol[2 * t] = H.cum_off[t];
+            ol[2 * t + 1] = H.cum_off[t + 1] - H.cum_off[t];
+        }
+    }
     if (!H.cum_ids.empty()) std::memcpy(host.data() + o_ids, H.cum_ids.data(), bytes_of(H.cum_ids));
     if (!H.bitmap.empty()) std::memcpy(host.data() + o_bm, H.bitmap.data(), bytes_of(H.bitmap));
     if (!H.grams.empty()) std::memcpy(host.data() + o_gr, H.grams.data(), bytes_of(H.grams));
@@ -132,6 +142,7 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
     D.row16 = row16 ? 1u : 0u;
     D.chain = reinterpret_cast<const GlopChain *>(base + o_chain);
     D.cum_off = reinterpret_cast<const uint32_t *>(base + o_cum);
+    D.outl = reinterpret_cast<const uint32_t *>(base + o_outl);
     D.cum_ids = reinterpret_cast<const uint32_t *>(base + o_ids);
     D.n_cum_ids = (uint32_t)H.cum_ids.size();
     D.bitmap = reinterpret_cast<const uint32_t *>(base + o_bm);
@@ -139,6 +150,7 @@ glop_status glop_compile(const uint8_t *pattern_bytes, const uint64_t *pattern_o
     h->blob_bytes = total;
     h->device = dev;
     h->smem_budget = opts ? opts->smem_budget_bytes : 0;
+    h->ksub = (opts && opts->chunk_subtiles == 2) ? 2u : 1u;
     glop_info &I = h->info;
     I.n_patterns = H.n_patterns;
     I.min_pattern_len = H.min_len;
@@ -199,6 +211,8 @@ static glop_status do_scan(glop_handle h, const uint8_t *d_text, uint64_t len, c
     L.ws_bytes = ws_bytes;
     L.stream = reinterpret_cast<cudaStream_t>(stream);
     L.smem_budget = h->smem_budget;
+    L.ksub = h->ksub;
+    L.ksub_used = &h->ksub_used;
     return (glop_status)glop::launch_scan(L);
 }
 
@@ -240,6 +254,8 @@ glop_status glop_scan_count(glop_handle h, const uint8_t *d_text, uint64_t len, 
     L.ws_bytes = workspace_bytes;
     L.stream = reinterpret_cast<cudaStream_t>(stream);
     L.smem_budget = h->smem_budget;
+    L.ksub = h->ksub;
+    L.ksub_used = &h->ksub_used;
     L.hist = reinterpret_cast<unsigned long long *>(d_hist);
     return (glop_status)glop::launch_scan(L);
 }
@@ -264,6 +280,9 @@ glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint
     uint64_t total;
     std::memcpy(&total, hdr + 4, 8);
     if (count) *count = total;
+    // a bounded wait that ran out comes first: phase B may then have met data phase A never wrote, and
+    // the checks that caught it are its consequence, not a separate fault
+    if (hdr[0] & glop::WS_TIMEOUT) return GLOP_ETIMEOUT;
     if (hdr[0] & glop::WS_INTERNAL) {
         std::fprintf(stderr, "glop: internal check failed at site %u (value %u)\n", hdr[11], hdr[12]);
         return GLOP_EINTERNAL;
@@ -385,6 +404,8 @@ glop_status scan_host_pieces(glop_handle h, const uint8_t *h_text, uint64_t len,
         L.ws_bytes = ws_bytes;
         L.stream = st;
         L.smem_budget = h->smem_budget;
+        L.ksub = h->ksub;
+        L.ksub_used = &h->ksub_used;
         L.own_len = b - a;
         L.base_off = (uint32_t)a;
         L.d_obase = reinterpret_cast<const unsigned long long *>(d_bases + k);
@@ -543,9 +564,11 @@ glop_status glop_tune(const uint8_t *pattern_bytes, const uint64_t *pattern_offs
             glop_handle h = nullptr;
             s = glop_compile(pattern_bytes, pattern_offsets, n_patterns, &o, &h);
             if (s != GLOP_OK) { cleanup(); return s; }
-            for (uint32_t budget : budgets) {
+            for (uint32_t budget : budgets)
+            for (uint32_t ks : {1u, 2u}) {
                 h->smem_budget = budget;
                 o.smem_budget_bytes = budget;
+                h->ksub = ks;
                 // size the output once (identical for every candidate), then warm up and time
                 if (!out) {
                     s = scan_once(h);
@@ -557,6 +580,8 @@ glop_status glop_tune(const uint8_t *pattern_bytes, const uint64_t *pattern_offs
                 }
                 s = scan_once(h);
                 if (s != GLOP_OK) { glop_destroy(h); cleanup(); return s; }
+                o.chunk_subtiles = h->ksub_used;  // (62 KiB chunks run as 31 KiB ones where two slots do not fit)
+                if (ks == 2 && h->ksub_used != 2) continue;
                 cudaEventRecord(e0, st);
                 for (uint32_t r = 0; r < repeats && s == GLOP_OK; ++r) s = scan_once(h);
                 cudaEventRecord(e1, st);

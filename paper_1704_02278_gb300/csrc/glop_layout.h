@@ -62,6 +62,7 @@ struct GlopDevAutomaton {
     const GlopChain *chain;        // [n_states - n_dense]
     uint32_t row16;                // 1: rows are uint16 (state | 0x8000 when terminal), else int32
     const uint32_t *cum_off;       // [n_states + 1] output list of each state
+    const uint32_t *outl;          // [2 * n_states] the same lists as (start, count) pairs, one 8-byte load each
     const uint32_t *cum_ids;       // pattern ids, ascending within a list
     uint32_t n_cum_ids;            // entries of cum_ids
     const uint32_t *bitmap;        // [(1 << bm_log2) / 32]; index i is bit (31 - i % 32) of word i / 32

@@ -32,6 +32,8 @@ struct ScanLaunch {
     uint64_t ws_bytes;
     cudaStream_t stream;
     uint32_t smem_budget;  // 0 = library default
+    uint32_t ksub = 1;     // sub-tiles each consumer warp takes from a staged chunk: 1 (31 KiB chunks) or 2 (62 KiB)
+    uint32_t *ksub_used = nullptr;  // if set: receives the ksub the launch used (2 falls back to 1 when it does not fit)
     unsigned long long *hist = nullptr;  // count-only mode: per-pattern counts (n_patterns); d_count = their sum
     // Pieces of a longer buffer (single buffer only): match starts in [0, own_len) (0 = len; bytes up to
     // len are look-ahead for walks), reported offsets + base_off, the first match written at output index

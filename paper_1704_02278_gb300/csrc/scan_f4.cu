@@ -1,0 +1,19 @@
+// scan_f4.cu -- instantiations of the scan kernel for 4-byte start-filter grams.
+#include "scan_kernel.cuh"
+
+namespace glop {
+namespace kern {
+
+int launch_f4(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub) {
+    if (deep)
+        return batch ? (r16 ? launch_t<4, true, true, true, 1>(kp, smem, grid, st) : launch_t<4, true, false, true, 1>(kp, smem, grid, st))
+                     : (r16 ? launch_t<4, false, true, true, 1>(kp, smem, grid, st) : launch_t<4, false, false, true, 1>(kp, smem, grid, st));
+    if (ksub == 2)
+        return batch ? (r16 ? launch_t<4, true, true, false, 2>(kp, smem, grid, st) : launch_t<4, true, false, false, 2>(kp, smem, grid, st))
+                     : (r16 ? launch_t<4, false, true, false, 2>(kp, smem, grid, st) : launch_t<4, false, false, false, 2>(kp, smem, grid, st));
+    return batch ? (r16 ? launch_t<4, true, true, false, 1>(kp, smem, grid, st) : launch_t<4, true, false, false, 1>(kp, smem, grid, st))
+                 : (r16 ? launch_t<4, false, true, false, 1>(kp, smem, grid, st) : launch_t<4, false, false, false, 1>(kp, smem, grid, st));
+}
+
+}  // namespace kern
+}  // namespace glop

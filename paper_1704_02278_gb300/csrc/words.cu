@@ -22,9 +22,9 @@ __global__ void words_kernel(const uint32_t *hdr, unsigned long long *h_words) {
     const uint32_t f = hdr[0];
     const unsigned long long total = (unsigned long long)hdr[4] | ((unsigned long long)hdr[5] << 32);
     uint32_t st = GLOP_OK;
-    if (f & glop::WS_INTERNAL) st = GLOP_EINTERNAL;
+    if (f & glop::WS_TIMEOUT) st = GLOP_ETIMEOUT;  // (as glop_scan_status: a timeout explains later checks)
+    else if (f & glop::WS_INTERNAL) st = GLOP_EINTERNAL;
     else if (f & glop::WS_EINVAL) st = GLOP_EINVAL;
-    else if (f & glop::WS_TIMEOUT) st = GLOP_ETIMEOUT;
     else if (f & glop::WS_OVERFLOW) st = GLOP_EOVERFLOW;
     h_words[0] = total;
     h_words[1] = st;
