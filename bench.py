@@ -45,20 +45,30 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("scan_kernel.cuh", "scan.cu")  # the scan kernel and its launcher
+
+
+def kernel_sha() -> str:
+    """sha256 prefix of the scan kernel's sources, as the committed ncu summaries record it."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1704_02278_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def profiled_value(workload: str, kind: str, key: str):
     """An integer ``key: N`` from the committed ncu summary profiles/scan_kernel_<workload>_<kind>.md, when
-    it was taken on the current scan.cu (its sha256 prefix matches); else None."""
-    import hashlib
+    it was taken on the current kernel sources (their sha256 prefix matches); else None."""
     import re
-    root = os.path.dirname(os.path.abspath(__file__))
-    path = os.path.join(root, "profiles", "scan_kernel_%s_%s.md" % (workload, kind))
-    src = os.path.join(root, "paper_1704_02278_gb300", "csrc", "scan.cu")
+    path = os.path.join(ROOT, "profiles", "scan_kernel_%s_%s.md" % (workload, kind))
     try:
         txt = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = kernel_sha()
     except OSError:
         return None
-    m_sha = re.search(r"scan\.cu sha256 prefix: ([0-9a-f]{16})", txt)
+    m_sha = re.search(r"kernel sources sha256 prefix: ([0-9a-f]{16})", txt)
     m_v = re.search(re.escape(key) + r": (\d+)", txt)
     if not m_sha or not m_v or m_sha.group(1) != sha:
         return None
@@ -67,22 +77,8 @@ def profiled_value(workload: str, kind: str, key: str):
 
 def profiled_traffic(workload: str):
     """DRAM bytes (read + write) per scan-kernel launch from the committed ncu summary of this workload,
-    when it was taken on the current scan.cu (its sha256 prefix matches); else None."""
-    import hashlib
-    import re
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
-                        "scan_kernel_%s_traffic.md" % workload)
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1704_02278_gb300", "csrc", "scan.cu")
-    try:
-        txt = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
-        return None
-    m_sha = re.search(r"scan\.cu sha256 prefix: ([0-9a-f]{16})", txt)
-    m_tr = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
-    if not m_sha or not m_tr or m_sha.group(1) != sha:
-        return None
-    return int(m_tr.group(1))
+    when it was taken on the current kernel sources; else None."""
+    return profiled_value(workload, "traffic", "traffic_bytes_per_launch")
 
 
 def read_stream_peak(dev, nbytes: int = 4 << 30, reps: int = 10):

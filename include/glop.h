@@ -183,6 +183,42 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
                             void *d_workspace, uint64_t workspace_bytes, glop_stream_t stream);
 
 /*
+ * glop_scan_batch_multi -- glop_scan_batch over segments that are scanned
+ * with different automata, in one persistent launch: a batch of requests for
+ * several resident pattern sets (the serving loop's continuous batching;
+ * the paper's library hands batches of logs to the GPU, Sec. 6, each searched
+ * as in Sec. 5 -- here with the rule set of its own request).
+ *
+ * handles       host, n_groups automata (1 .. GLOP_BATCH_MAX_GROUPS) of the
+ *               current device, each with at least one pattern, all of one
+ *               kernel kind (equal glop_batch_multi_kind values).
+ * group_start   host, n_groups + 1 byte offsets: group g is the text
+ *               [group_start[g], group_start[g + 1]), scanned with handles[g].
+ *               group_start[0] = 0, group_start[n_groups] = text_len,
+ *               non-decreasing, every group_start[g] a multiple of 1024 (the
+ *               scan's sub-tile) and, on the device, equal to some
+ *               d_seg_offsets value, so that no segment straddles two groups
+ *               (else glop_scan_status returns GLOP_EINVAL and *d_count = 0).
+ *               Bytes between segments are not possible (segments are
+ *               contiguous): a caller that pads a group to 1024 bytes gives
+ *               the padding a segment of its own and ignores its matches.
+ * Other arguments, results, ordering (by segment, offset, pattern id; pattern
+ * ids of the segment's own automaton) and errors as for glop_scan_batch; the
+ * workspace size is glop_batch_workspace_size's.  Each thread block of the
+ * launch serves one group and stages that group's tables once.
+ */
+#define GLOP_BATCH_MAX_GROUPS 8
+glop_status glop_scan_batch_multi(const glop_handle *handles, uint32_t n_groups, const uint64_t *group_start,
+                                  const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
+                                  uint32_t n_segments, glop_batch_match *d_matches, uint64_t capacity,
+                                  uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes,
+                                  glop_stream_t stream);
+/* The kernel kind of an automaton (its start filter's gram class and row
+ * width): handles can share one glop_scan_batch_multi launch when their kinds
+ * are equal.  Host only. */
+glop_status glop_batch_multi_kind(glop_handle h, uint32_t *kind);
+
+/*
  * glop_scan_status -- wait for stream, then report the outcome of the last
  * scan that used d_workspace: GLOP_OK, GLOP_EOVERFLOW (more matches than
  * capacity), GLOP_ETIMEOUT (a bounded in-kernel wait ran out), GLOP_EINVAL

@@ -39,7 +39,7 @@ SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_w
            "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split",
            "glop_count_workspace_size", "glop_scan_count", "glop_scan_host_plan", "glop_scan_words",
            "glop_ingest_create", "glop_ingest_feed", "glop_ingest_flush", "glop_ingest_reset", "glop_ingest_info",
-           "glop_ingest_destroy"]
+           "glop_ingest_destroy", "glop_scan_batch_multi", "glop_batch_multi_kind"]
 
 
 class IngestResult(ctypes.Structure):
@@ -99,6 +99,10 @@ def lib():
         L.glop_scan.argtypes = [vp, vp, u64, vp, u64, vp, vp, u64, vp]
         L.glop_scan_batch.restype = ctypes.c_int
         L.glop_scan_batch.argtypes = [vp, vp, u64, vp, u32, vp, u64, vp, vp, u64, vp]
+        L.glop_scan_batch_multi.restype = ctypes.c_int
+        L.glop_scan_batch_multi.argtypes = [vp, u32, vp, vp, u64, vp, u32, vp, u64, vp, vp, u64, vp]
+        L.glop_batch_multi_kind.restype = ctypes.c_int
+        L.glop_batch_multi_kind.argtypes = [vp, ctypes.POINTER(u32)]
         L.glop_scan_status.restype = ctypes.c_int
         L.glop_scan_status.argtypes = [vp, vp, ctypes.POINTER(u64)]
         L.glop_scan_host_staging_size.restype = ctypes.c_int
@@ -432,6 +436,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def batch_multi_kind(a: "Automaton") -> int:
+    """The kernel kind of an automaton: automata of equal kinds can share one scan_batch_multi launch."""
+    k = ctypes.c_uint32()
+    _check(lib().glop_batch_multi_kind(a.handle, ctypes.byref(k)), "glop_batch_multi_kind")
+    return int(k.value)
+
+
+def scan_batch_multi_into(automata, group_start, text, seg_offsets, matches, count, workspace, stream=None) -> None:
+    """Queue one batch scan over segments of several automata (glop_scan_batch_multi): group g is the text
+    [group_start[g], group_start[g + 1]) (host ints, multiples of 1024, each the start of a segment),
+    scanned with automata[g]; writes (segment, offset, pattern_id) rows to ``matches`` and the total to
+    ``count``.  Asynchronous."""
+    n = len(automata)
+    hs = (ctypes.c_void_p * n)(*[a.handle.value for a in automata])
+    gs = np.ascontiguousarray(group_start, dtype=np.uint64)
+    cap = matches.shape[0] if matches is not None else 0
+    nseg = seg_offsets.numel() - 1
+    _check(lib().glop_scan_batch_multi(hs, n, gs.ctypes.data, text.data_ptr() if text.numel() else None,
+                                       text.numel(), seg_offsets.data_ptr(), nseg,
+                                       matches.data_ptr() if cap else None, cap, count.data_ptr(),
+                                       workspace.data_ptr(), workspace.numel(), _stream_handle(stream)),
+           "glop_scan_batch_multi")
 
 
 def _opts_dict(o: glop_compile_opts) -> dict:

@@ -269,6 +269,60 @@ glop_status glop_scan_batch(glop_handle h, const uint8_t *d_text, uint64_t text_
                    workspace_bytes, stream);
 }
 
+static_assert(GLOP_BATCH_MAX_GROUPS == glop::kMaxBatchGroups, "one limit for the header and the kernel");
+
+glop_status glop_scan_batch_multi(const glop_handle *handles, uint32_t n_groups, const uint64_t *group_start,
+                                  const uint8_t *d_text, uint64_t text_len, const uint64_t *d_seg_offsets,
+                                  uint32_t n_segments, glop_batch_match *d_matches, uint64_t capacity,
+                                  uint64_t *d_count, void *d_workspace, uint64_t workspace_bytes,
+                                  glop_stream_t stream) {
+    if (!handles || !group_start || n_groups == 0 || n_groups > GLOP_BATCH_MAX_GROUPS) return GLOP_EINVAL;
+    if (!d_seg_offsets || (reinterpret_cast<uintptr_t>(d_seg_offsets) & 7)) return GLOP_EINVAL;
+    if (d_matches && (reinterpret_cast<uintptr_t>(d_matches) & 3)) return GLOP_EINVAL;
+    if (!d_count || !d_workspace || (text_len && !d_text) || (capacity && !d_matches)) return GLOP_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_workspace) & 15) || (reinterpret_cast<uintptr_t>(d_count) & 7)) return GLOP_EINVAL;
+    if (workspace_bytes < glop::workspace_bytes(text_len, true)) return GLOP_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GLOP_ECUDA;
+    // group bytes: from 0 to text_len, non-decreasing, every start on a sub-tile boundary
+    if (group_start[0] != 0 || group_start[n_groups] != text_len) return GLOP_EINVAL;
+    GlopDevAutomaton as[GLOP_BATCH_MAX_GROUPS];
+    for (uint32_t g = 0; g < n_groups; ++g) {
+        const glop_handle h = handles[g];
+        if (!h || h->device != dev || h->dev.n_patterns == 0) return GLOP_EINVAL;
+        if (group_start[g + 1] < group_start[g] || group_start[g] % glop::kSubTile) return GLOP_EINVAL;
+        // one kernel variant for every group: the start filter's kind and the row width
+        const GlopDevAutomaton &a = h->dev, &a0 = handles[0]->dev;
+        auto kind = [](uint32_t gram) { return gram == 0 ? 0u : gram == 4 ? 4u : 8u; };
+        if (kind(a.gram_len) != kind(a0.gram_len) || a.row16 != a0.row16) return GLOP_EINVAL;
+        as[g] = a;
+    }
+    glop::ScanLaunch L;
+    L.A = &as[0];
+    L.text = d_text;
+    L.len = text_len;
+    L.seg = d_seg_offsets;
+    L.n_seg = n_segments;
+    L.out = d_matches;
+    L.capacity = capacity;
+    L.d_count = d_count;
+    L.ws = d_workspace;
+    L.ws_bytes = workspace_bytes;
+    L.stream = reinterpret_cast<cudaStream_t>(stream);
+    L.smem_budget = handles[0]->smem_budget;
+    L.n_groups = n_groups;
+    L.group_A = as;
+    L.group_start = group_start;
+    return (glop_status)glop::launch_scan(L);
+}
+
+glop_status glop_batch_multi_kind(glop_handle h, uint32_t *kind) {
+    if (!h || !kind) return GLOP_EINVAL;
+    const uint32_t g = h->dev.gram_len;
+    *kind = (g == 0 ? 0u : g == 4 ? 4u : 8u) | (h->dev.row16 ? 0x100u : 0u);
+    return GLOP_OK;
+}
+
 glop_status glop_scan_status(const void *d_workspace, glop_stream_t stream, uint64_t *count) {
     // NULL: the scratch array of glop_scan_noalloc on the current device
     if (!d_workspace) d_workspace = glop::noalloc_scratch_of_current_device();

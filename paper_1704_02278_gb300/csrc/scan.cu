@@ -10,8 +10,14 @@ namespace kern {
 // ---------------------------------------------------------------- kernels
 // Zero the workspace header; for batches also check the segment table and
 // find, for every sub-tile, the last segment starting at or before it.
+// Several automata in one batch: the byte where each group starts.
+struct GroupStarts {
+    uint32_t n;
+    uint64_t start[kMaxBatchGroups + 1];
+};
+
 __global__ void init_kernel(uint32_t *hdr, uint32_t *tile_seg, uint64_t n_sub, const uint64_t *seg, uint32_t n_seg,
-                            uint64_t len, unsigned long long *d_count, int zero_header, int nothing) {
+                            uint64_t len, unsigned long long *d_count, int zero_header, int nothing, GroupStarts gs) {
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
     if (zero_header && tid < kHeaderBytes / 4) hdr[tid] = 0;
@@ -21,6 +27,17 @@ __global__ void init_kernel(uint32_t *hdr, uint32_t *tile_seg, uint64_t n_sub, c
     for (uint64_t s = tid; s < n_seg; s += nthr) {
         const uint64_t a = seg[s], b = seg[s + 1];
         if (b < a || b - a > 0xFFFFFFFFull || b > len) bad = true;
+    }
+    // several automata: every group after the first must start where a segment starts (no segment
+    // straddles two groups)
+    if (tid >= 1 && tid < gs.n) {
+        const uint64_t x = gs.start[tid];
+        uint32_t lo = 0, hi = n_seg;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (seg[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        if (seg[lo] != x) bad = true;
     }
     if (bad) {
         atomicOr(hdr, WS_EINVAL);
@@ -106,6 +123,11 @@ int launch_scan(const ScanLaunch &L) {
     const bool batch = L.seg != nullptr;
     const bool count = L.hist != nullptr;  // count-only mode (single buffer): hits per state, no records
     if (count && batch) return 1;
+    // several automata (batches only): na groups, automaton ga(g) for group g
+    const uint32_t ng = L.n_groups;
+    if (ng && (!batch || ng > kMaxBatchGroups || !L.group_A || !L.group_start)) return 1;
+    const uint32_t na = ng ? ng : 1;
+    auto ga = [&](uint32_t g) -> const GlopDevAutomaton & { return ng ? L.group_A[g] : A; };
     const uint64_t own_len = L.own_len ? std::min(L.own_len, L.len) : L.len;
     if (batch && own_len != L.len) return 1;
     const uint64_t n_sub = (own_len + SUB - 1) / SUB;
@@ -118,7 +140,9 @@ int launch_scan(const ScanLaunch &L) {
                   cudaMemsetAsync(L.d_count, 0, 8, L.stream) != cudaSuccess ||
                   cudaMemsetAsync(hits, 0, 4ull * A.n_states, L.stream) != cudaSuccess))
         return 4;
-    const bool nothing = (A.n_patterns == 0) || n_sub == 0 || (batch && L.n_seg == 0);
+    uint32_t all_patterns = 0;
+    for (uint32_t g = 0; g < na; ++g) all_patterns += ga(g).n_patterns ? 1u : 0u;
+    const bool nothing = all_patterns == 0 || n_sub == 0 || (batch && L.n_seg == 0);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 4;
     const DevProps pr = props_of(dev);
@@ -130,10 +154,13 @@ int launch_scan(const ScanLaunch &L) {
         const uint64_t work = std::max<uint64_t>(n_sub + 1, batch ? L.n_seg : 0);
         uint32_t blocks = (uint32_t)std::min<uint64_t>((work + 255) / 256, (uint64_t)pr.sms * 8);
         if (blocks == 0) blocks = 1;
+        GroupStarts gs{};
+        gs.n = ng;
+        for (uint32_t g = 0; g <= ng && ng; ++g) gs.start[g] = L.group_start[g];
         init_kernel<<<blocks, 256, 0, L.stream>>>(hdr, reinterpret_cast<uint32_t *>(ws + W.tile_seg), nothing ? 0 : n_sub,
                                                    batch ? L.seg : nullptr, batch ? L.n_seg : 0, L.len,
                                                    reinterpret_cast<unsigned long long *>(L.d_count), batch ? 0 : 1,
-                                                   nothing ? 1 : 0);
+                                                   nothing ? 1 : 0, gs);
         if (cudaGetLastError() != cudaSuccess) return 4;
     }
     if (nothing) {
@@ -167,7 +194,9 @@ int launch_scan(const ScanLaunch &L) {
     kp.records = count ? nullptr : reinterpret_cast<uint32_t *>(ws + W.records);
     kp.state_hits = hits;
     kp.n_sub = n_sub;
-    uint32_t halo = A.max_len > 1 ? A.max_len - 1 : 0;
+    uint32_t max_len = 0;
+    for (uint32_t g = 0; g < na; ++g) max_len = std::max(max_len, ga(g).max_len);
+    uint32_t halo = max_len > 1 ? max_len - 1 : 0;
     halo = std::max<uint32_t>(16, align_up(std::min(halo, HALO_CAP), 16));
     kp.halo = halo;
     kp.aligned = (reinterpret_cast<uintptr_t>(L.text) & 15) == 0;
@@ -182,20 +211,32 @@ int launch_scan(const ScanLaunch &L) {
 
     // shared memory: class map, bitmap, gram table, block state, ring, hot rows.
     // The ring has 3 slots, or 2 when that is what lets every walked dense row stay on chip.
+    // (several automata: one layout for every group -- the largest bitmap and gram table -- and each
+    // group's hot rows in what is left)
     const uint32_t budget = (uint32_t)pr.smem_optin;
-    const uint32_t row_bytes = A.n_classes * (A.row16 ? 2u : 4u);
-    const uint32_t hot_avail = A.n_dense > A.hot_lo ? A.n_dense - A.hot_lo : 0;
+    auto row_bytes_of = [&](uint32_t g) { return ga(g).n_classes * (ga(g).row16 ? 2u : 4u); };
+    auto hot_avail_of = [&](uint32_t g) { return ga(g).n_dense > ga(g).hot_lo ? ga(g).n_dense - ga(g).hot_lo : 0u; };
+    const uint32_t row_bytes = row_bytes_of(0);
+    const uint32_t hot_avail = hot_avail_of(0);
+    uint32_t bitmap_bytes = 0, gram_bytes = 0;
+    for (uint32_t g = 0; g < na; ++g) {
+        const GlopDevAutomaton &B = ga(g);
+        if (B.gram_len) {
+            bitmap_bytes = std::max(bitmap_bytes, (1u << B.bm_log2) / 8);
+            gram_bytes = std::max(gram_bytes, (1u << B.ht_log2) * (B.gram_len == 4 ? 8u : 16u));
+        }
+    }
+    bool rows_short = false;  // some group's walked dense rows do not all fit on chip
     auto carve = [&](uint32_t nstage) -> uint32_t {
         kp.nstage = nstage;
         uint32_t off = 384;
         kp.off_bitmap = off;
-        if (A.gram_len) off += (1u << A.bm_log2) / 8;
+        off += bitmap_bytes;
         off = align_up(off, 128);
         kp.off_grams = off;
-        const uint32_t gram_bytes = A.gram_len ? (1u << A.ht_log2) * (A.gram_len == 4 ? 8u : 16u) : 0u;
         const uint32_t fixed_after = align_up((uint32_t)sizeof(CtaMisc), 128) + nstage * kp.slot_bytes + 32 * QBYTES +
                                      (count ? 8 * HCACHE : 0);
-        kp.grams_in_smem = (A.gram_len && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
+        kp.grams_in_smem = (gram_bytes && gram_bytes <= 32768 && off + gram_bytes + fixed_after <= budget) ? 1u : 0u;
         if (kp.grams_in_smem) off += gram_bytes;
         off = align_up(off, 128);
         kp.off_misc = off;
@@ -211,7 +252,16 @@ int launch_scan(const ScanLaunch &L) {
         uint32_t avail = budget > off + 32 ? budget - off - 32 : 0;
         if (L.smem_budget) avail = std::min(avail, L.smem_budget);
         kp.hot_n = std::min<uint32_t>(hot_avail, row_bytes ? avail / row_bytes : 0);
-        off += align_up(kp.hot_n * row_bytes + 16, 16);
+        uint32_t rows_max = kp.hot_n * row_bytes;
+        rows_short = kp.hot_n < hot_avail;
+        for (uint32_t g = 0; g < ng; ++g) {
+            const uint32_t rb = row_bytes_of(g), h = std::min<uint32_t>(hot_avail_of(g), rb ? avail / rb : 0);
+            kp.grp.hot_n[g] = h;
+            kp.grp.grams_in_smem[g] = ga(g).gram_len ? kp.grams_in_smem : 0u;
+            rows_max = std::max(rows_max, h * rb);
+            rows_short = rows_short || h < hot_avail_of(g);
+        }
+        off += align_up(rows_max + 16, 16);
         return off;
     };
     // (3 slots unless 2 let every walked dense row on chip, or 3 do not fit beside the tables at all)
@@ -219,25 +269,49 @@ int launch_scan(const ScanLaunch &L) {
         kp.ksub = ksub;
         kp.slot_bytes = align_up(CHUNK * ksub + halo + 64, 128);
         uint32_t smem = carve(NSTAGE);
-        if ((kp.hot_n < hot_avail && !L.smem_budget) || smem > budget) {
+        if ((rows_short && !L.smem_budget) || smem > budget) {
             const uint32_t smem2 = carve(2);
-            if ((kp.hot_n < hot_avail || smem2 > budget) && smem <= budget) smem = carve(NSTAGE);
+            if ((rows_short || smem2 > budget) && smem <= budget) smem = carve(NSTAGE);
             else smem = smem2;
         }
         return smem;
     };
     // 62 KiB chunks when asked for, the walks stay within the staged halo (no DEEP) and two such ring
     // slots fit beside the tables; else 31 KiB
-    const bool deep = A.max_len > 1 && A.max_len - 1 > halo;
-    uint32_t smem = carve_ring(L.ksub == 2 && !deep ? 2u : 1u);
+    const bool deep = max_len > 1 && max_len - 1 > halo;
+    uint32_t smem = carve_ring(L.ksub == 2 && !deep && !ng ? 2u : 1u);
     if (smem > budget && kp.ksub == 2) smem = carve_ring(1);
     if (smem > budget) return 7;
     const uint64_t n_chunks = (n_sub + NCONS * kp.ksub - 1) / (NCONS * kp.ksub);
     kp.n_chunks = n_chunks;
     if (L.ksub_used) *L.ksub_used = kp.ksub;
     if (PB * 8 > kp.nstage * kp.slot_bytes) return 7;
-    uint32_t grid = (uint32_t)std::min<uint64_t>(n_chunks, (uint64_t)std::min(pr.sms, (int)kMaxGrid));
+    const uint32_t max_grid = (uint32_t)std::min(pr.sms, (int)kMaxGrid);
+    uint32_t grid = (uint32_t)std::min<uint64_t>(n_chunks, (uint64_t)max_grid);
     if (grid == 0) grid = 1;
+    kp.grp.n = ng;
+    if (ng) {
+        // group g: sub-tiles [sub[g], sub[g + 1]) and blocks [blk[g], blk[g + 1]), at least one block each,
+        // the rest shared in proportion to the groups' chunks
+        uint64_t gch[kMaxBatchGroups], tot = 0;
+        for (uint32_t g = 0; g < ng; ++g) {
+            kp.grp.A[g] = L.group_A[g];
+            kp.grp.sub[g] = L.group_start[g] / SUB;
+            gch[g] = (L.group_start[g + 1] - L.group_start[g] + CHUNK - 1) / CHUNK;
+            tot += gch[g];
+        }
+        kp.grp.sub[ng] = n_sub;
+        grid = (uint32_t)std::max<uint64_t>(ng, std::min<uint64_t>(tot, max_grid));
+        if (grid > max_grid) return 1;
+        uint32_t extra = grid - ng, given = 0, nb[kMaxBatchGroups];
+        for (uint32_t g = 0; g < ng; ++g) {
+            nb[g] = 1 + (tot ? (uint32_t)(gch[g] * extra / tot) : 0u);
+            given += nb[g];
+        }
+        for (uint32_t g = 0; given < grid; g = (g + 1) % ng) { ++nb[g]; ++given; }
+        kp.grp.blk[0] = 0;
+        for (uint32_t g = 0; g < ng; ++g) kp.grp.blk[g + 1] = kp.grp.blk[g] + nb[g];
+    }
     kp.rec_cap_cta = (uint32_t)std::min<uint64_t>(W.rec_slots / grid, 0xFFFFFFF0ull / grid);
     // a single-buffer record holds the terminal state in 22 bits: larger automata keep no records (phase B
     // walks every sub-tile again)
@@ -246,9 +320,10 @@ int launch_scan(const ScanLaunch &L) {
 
     const bool r16 = A.row16 != 0;
     auto dispatch = [&]() -> int {
-        if (A.gram_len == 0) return launch_f0(kp, smem, grid, L.stream, batch, r16, deep, kp.ksub);
-        if (A.gram_len == 4) return launch_f4(kp, smem, grid, L.stream, batch, r16, deep, kp.ksub);
-        return launch_f8(kp, smem, grid, L.stream, batch, r16, deep, kp.ksub);
+        const bool multi = ng != 0;
+        if (A.gram_len == 0) return launch_f0(kp, smem, grid, L.stream, batch, r16, deep, kp.ksub, multi);
+        if (A.gram_len == 4) return launch_f4(kp, smem, grid, L.stream, batch, r16, deep, kp.ksub, multi);
+        return launch_f8(kp, smem, grid, L.stream, batch, r16, deep, kp.ksub, multi);
     };
     const int rc = dispatch();
     if (rc || !count) return rc;

@@ -18,6 +18,7 @@ constexpr uint32_t kConsumers = 31;
 constexpr uint32_t kChunk = kSubTile * kConsumers;
 constexpr uint32_t kHeaderBytes = 256;
 constexpr uint32_t kMaxGrid = 1024;
+constexpr uint32_t kMaxBatchGroups = 8;  // automata in one batch launch
 
 struct ScanLaunch {
     const GlopDevAutomaton *A;  // descriptor with device pointers (host copy)
@@ -34,6 +35,13 @@ struct ScanLaunch {
     uint32_t smem_budget;  // 0 = library default
     uint32_t ksub = 1;     // sub-tiles each consumer warp takes from a staged chunk: 1 (31 KiB chunks) or 2 (62 KiB)
     uint32_t *ksub_used = nullptr;  // if set: receives the ksub the launch used (2 falls back to 1 when it does not fit)
+    // Several automata in one batch launch: n_groups > 0 groups of segments, group g starting at byte
+    // group_start[g] (a multiple of kSubTile; group_start[n_groups] = len) and scanned with group_A[g]
+    // (host arrays).  A then points at group_A[0]; every group must share its start-filter kind and row
+    // width (the kernel variant).
+    uint32_t n_groups = 0;
+    const GlopDevAutomaton *group_A = nullptr;
+    const uint64_t *group_start = nullptr;
     unsigned long long *hist = nullptr;  // count-only mode: per-pattern counts (n_patterns); d_count = their sum
     // Pieces of a longer buffer (single buffer only): match starts in [0, own_len) (0 = len; bytes up to
     // len are look-ahead for walks), reported offsets + base_off, the first match written at output index

@@ -4,7 +4,11 @@
 namespace glop {
 namespace kern {
 
-int launch_f4(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub) {
+int launch_f4(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub,
+              bool multi) {
+    if (multi)  // several automata: batches, 31 KiB chunks
+        return deep ? (r16 ? launch_t<4, true, true, true, 1, true>(kp, smem, grid, st) : launch_t<4, true, false, true, 1, true>(kp, smem, grid, st))
+                    : (r16 ? launch_t<4, true, true, false, 1, true>(kp, smem, grid, st) : launch_t<4, true, false, false, 1, true>(kp, smem, grid, st));
     if (deep)
         return batch ? (r16 ? launch_t<4, true, true, true, 1>(kp, smem, grid, st) : launch_t<4, true, false, true, 1>(kp, smem, grid, st))
                      : (r16 ? launch_t<4, false, true, true, 1>(kp, smem, grid, st) : launch_t<4, false, false, true, 1>(kp, smem, grid, st));

@@ -82,6 +82,22 @@ struct CtaMisc {
     unsigned long long segl[32][SEGW + 1];
     uint32_t seg_a[32], seg_L[32];
     uint32_t slot_seg[NSTAGE][2 * NCONS + 2];  // batches: first segment of each sub-tile of the slot's chunk (+ the next)
+    GlopDevAutomaton a_s;  // several automata in one launch: the automaton of this block's group
+};
+
+// Several automata in one batch launch (a batch of requests for several
+// resident pattern sets): group g is the segments of sub-tiles
+// [sub[g], sub[g + 1]) (its bytes start on a sub-tile boundary), scanned with
+// automaton A[g] by blocks [blk[g], blk[g + 1]) -- each block stages its own
+// group's tables once and takes chunk tickets of that group alone, so no
+// block ever switches automata.
+constexpr uint32_t kMaxGroups = kMaxBatchGroups;
+struct Groups {
+    uint32_t n;  // 0: one automaton (KParams::A)
+    uint32_t blk[kMaxGroups + 1];
+    uint32_t hot_n[kMaxGroups], grams_in_smem[kMaxGroups];
+    uint64_t sub[kMaxGroups + 1];
+    GlopDevAutomaton A[kMaxGroups];
 };
 
 struct KParams {
@@ -112,6 +128,7 @@ struct KParams {
     long long spin_budget;
     uint32_t barrier_extra;  // fault injection for tests: grid barriers wait for this many absent blocks
     unsigned long long withhold_chunk;  // fault injection for tests: this chunk is never staged (~0: none)
+    Groups grp;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -350,19 +367,37 @@ __device__ __forceinline__ bool step(const GlopDevAutomaton &A, const uint8_t *c
     return false;
 }
 
-template <int FILT, bool BATCH, bool ROW16, bool DEEP, uint32_t KSUB>
-__global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
+// (The parameter block is __grid_constant__: with several automata a block
+// reads its group's descriptor by address, and that must not copy the
+// parameters to local memory.)
+template <int FILT, bool BATCH, bool ROW16, bool DEEP, uint32_t KSUB, bool MULTI>
+__global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant__ KParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
-    const GlopDevAutomaton &A = p.A;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (BATCH && (ld_acquire32(p.hdr) & WS_EINVAL)) return;
+    // this block's automaton: the launch's, or (several automata) its group's, copied to shared memory
+    uint32_t grp = 0;
+    if (MULTI) {
+        while (grp + 1 < p.grp.n && blockIdx.x >= p.grp.blk[grp + 1]) ++grp;
+        CtaMisc *m0 = reinterpret_cast<CtaMisc *>(smem + p.off_misc);
+        constexpr uint32_t NW = sizeof(GlopDevAutomaton) / 4;
+        if (tid < NW) reinterpret_cast<uint32_t *>(&m0->a_s)[tid] = reinterpret_cast<const uint32_t *>(&p.grp.A[grp])[tid];
+        __syncthreads();
+    }
+    const GlopDevAutomaton &A = MULTI ? reinterpret_cast<CtaMisc *>(smem + p.off_misc)->a_s : p.A;
+    const uint32_t hot_n = MULTI ? p.grp.hot_n[grp] : p.hot_n;
+    const uint32_t grams_in_smem = MULTI ? p.grp.grams_in_smem[grp] : p.grams_in_smem;
+    // sub-tiles and chunks of this block's group (the whole text with one automaton)
+    const uint64_t sub0 = MULTI ? p.grp.sub[grp] : 0ull, sub_end = MULTI ? p.grp.sub[grp + 1] : p.n_sub;
+    const uint64_t n_chunks = MULTI ? (sub_end - sub0 + NCONS * KSUB - 1) / (NCONS * KSUB) : p.n_chunks;
+    unsigned long long *ticket = reinterpret_cast<unsigned long long *>(p.hdr + (MULTI ? 16 + 2 * grp : 2));
 
     uint8_t *cls_s = smem;
     uint32_t *fb_s = reinterpret_cast<uint32_t *>(smem + 256);
     const uint32_t *bm_s = reinterpret_cast<const uint32_t *>(smem + p.off_bitmap);
     // 4-byte grams: the shared-memory copy keeps (key_lo, val) only, 8 bytes a slot
     const GlopGramSlot *grams =
-        p.grams_in_smem ? reinterpret_cast<const GlopGramSlot *>(smem + p.off_grams) : A.grams;
+        grams_in_smem ? reinterpret_cast<const GlopGramSlot *>(smem + p.off_grams) : A.grams;
     const uint2 *grams8 = reinterpret_cast<const uint2 *>(smem + p.off_grams);
     const void *rows_s =
         smem + p.off_rows + (((size_t)A.hot_lo * A.n_classes * (ROW16 ? 2u : 4u)) & 15);
@@ -379,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             const uint4 *src = reinterpret_cast<const uint4 *>(A.bitmap);
             uint4 *dst = reinterpret_cast<uint4 *>(smem + p.off_bitmap);
             for (uint32_t i = tid; i < (1u << A.bm_log2) / 128; i += THREADS) dst[i] = __ldg(src + i);
-            if (p.grams_in_smem) {
+            if (grams_in_smem) {
                 const uint4 *gs = reinterpret_cast<const uint4 *>(A.grams);
                 if (FILT == 4) {
                     uint2 *gd = reinterpret_cast<uint2 *>(smem + p.off_grams);
@@ -397,7 +432,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         const uint32_t esz = ROW16 ? 2u : 4u;
         const size_t start = (size_t)A.hot_lo * A.n_classes * esz;
         const uint32_t lead = (uint32_t)(start & 15);
-        const uint32_t n16 = (lead + p.hot_n * A.n_classes * esz + 15) / 16;
+        const uint32_t n16 = (lead + hot_n * A.n_classes * esz + 15) / 16;
         const uint4 *rsrc = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(A.rows) + start - lead);
         uint4 *rdst = reinterpret_cast<uint4 *>(smem + p.off_rows);
         for (uint32_t i = tid; i < n16; i += THREADS) rdst[i] = __ldg(rsrc + i);
@@ -453,7 +488,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             uint32_t h = w0 * GLOP_HASH_M0;
             if (FILT == 8) h ^= w1 * GLOP_HASH_M1;
             uint32_t slot = glop_table_slot(h, A.ht_log2);
-            if (FILT == 4 && p.grams_in_smem) {
+            if (FILT == 4 && grams_in_smem) {
                 while (true) {
                     const uint2 e = grams8[slot];
                     if (!e.y) return 0u;
@@ -723,8 +758,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                     nxt += __popc(wm);
                     if (!__any_sync(FULL, have)) break;
                     // the direct (re-walk) mode reads the text from global memory: no staged bytes
-                    const bool fin = have && (direct ? step<ROW16, true>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr)
-                                                     : step<ROW16, DEEP>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr));
+                    const bool fin = have && (direct ? step<ROW16, true>(A, cls_s, rows_s, hot_n, v, st, pos, endw, t, p.hdr)
+                                                     : step<ROW16, DEEP>(A, cls_s, rows_s, hot_n, v, st, pos, endw, t, p.hdr));
                     if (fin) {
                         qst[qi] = t;
                         have = false;
@@ -749,8 +784,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                         uint32_t t = (val & GLOP_TERM) ? st : 0u;
                         pos = qoff[i] + g;
                         const uint32_t endw = BATCH ? qend[i] : endsub;
-                        const bool fin = direct ? step<ROW16, true>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr)
-                                                : step<ROW16, DEEP>(A, cls_s, rows_s, p.hot_n, v, st, pos, endw, t, p.hdr);
+                        const bool fin = direct ? step<ROW16, true>(A, cls_s, rows_s, hot_n, v, st, pos, endw, t, p.hdr)
+                                                : step<ROW16, DEEP>(A, cls_s, rows_s, hot_n, v, st, pos, endw, t, p.hdr);
                         qst[i] = t;
                         cont = !fin;
                     }
@@ -862,10 +897,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 issued &= ~(1u << slot);
             }
             unsigned long long k = 0;
-            if (lane == 0) k = atomicAdd(reinterpret_cast<unsigned long long *>(p.hdr + 2), 1ull);
+            if (lane == 0) k = atomicAdd(ticket, 1ull);
             k = shfl64(k, 0);
             uint8_t *dst = ring + (size_t)slot * p.slot_bytes;
-            if (k >= p.n_chunks) {
+            if (k >= n_chunks) {
                 if (lane == 0) {
                     mc->slot_tile[slot] = END_TICKET;
                     mbar_arrive(&mc->full[slot]);
@@ -875,7 +910,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             // (test hook: a chunk that is never staged, so every consumer's wait for it runs out)
             if (k == p.withhold_chunk) continue;
             const uint32_t csubs = NCONS * KSUB;  // sub-tiles per chunk
-            const uint64_t c0 = k * csubs * SUB;
+            const uint64_t c0 = (sub0 + k * csubs) * SUB;
             const uint32_t n_stage = (uint32_t)min((uint64_t)(csubs * SUB + p.halo), p.len - c0);
             const uint32_t bulk = p.aligned ? (n_stage & ~15u) : 0u;
             for (uint32_t y = bulk + lane; y < n_stage; y += 32)
@@ -884,7 +919,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             // start their segment-boundary loads without a round trip
             if (BATCH)
                 for (uint32_t q = lane; q <= csubs; q += 32)
-                    mc->slot_seg[slot][q] = __ldg(p.tile_seg + min((uint64_t)(k * csubs + q), (uint64_t)p.n_sub));
+                    mc->slot_seg[slot][q] = __ldg(p.tile_seg + min((uint64_t)(sub0 + k * csubs + q), (uint64_t)p.n_sub));
             __syncwarp();
             if (lane == 0) {
                 mc->slot_tile[slot] = k;
@@ -928,8 +963,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             // the warp's ksub consecutive sub-tiles of the chunk
             for (uint32_t u = 0; u < KSUB; ++u) {
                 const uint32_t w = cw * KSUB + u;  // sub-tile position in the chunk
-                const uint64_t j = k * NCONS * KSUB + w;
-                if (j >= p.n_sub) break;
+                const uint64_t j = sub0 + k * NCONS * KSUB + w;
+                if (j >= sub_end) break;
                 const uint32_t ns = mc->slot_nstage[slot];
                 TextView v;
                 v.buf = ring + (size_t)slot * p.slot_bytes + w * SUB;
@@ -966,8 +1001,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
         uint32_t *dst = reinterpret_cast<uint32_t *>(ring + PB * 8);
         for (uint32_t i = tid; i < n_ids_s; i += THREADS) dst[i] = __ldg(A.cum_ids + i);
     }
-    const uint64_t R = (p.n_sub + G - 1) / G;
-    const uint64_t ra = min(p.n_sub, (uint64_t)blockIdx.x * R), rb = min(p.n_sub, ra + R);
+    // this block's static range of sub-tiles (several automata: a share of its own group's, so that
+    // records, re-walks and output lists use the tables this block staged; blocks and groups are in
+    // text order, so block order is still sub-tile order)
+    uint64_t ra, rb;
+    {
+        const uint64_t b0 = MULTI ? p.grp.blk[grp] : 0u, nb = MULTI ? p.grp.blk[grp + 1] - b0 : G;
+        const uint64_t R = (sub_end - sub0 + nb - 1) / nb;
+        ra = min(sub_end, sub0 + (blockIdx.x - b0) * R);
+        rb = min(sub_end, ra + R);
+    }
     {
         unsigned long long sum = 0;
         for (uint64_t j = ra + tid; j < rb; j += THREADS)
@@ -1046,32 +1089,43 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
             if (x < np) GLOP_CK(p.hdr, p0 + x < p.n_sub, 32, p0 + x) d = __ldcg(reinterpret_cast<const uint4 *>(p.desc + p0 + x));
             return d;
         };
-        // record r of sub-tile j (0s past its end) as (f0, f1, lo, c): the reported
-        // offset (batches: segment, offset in it) and the output list.  Every index
-        // taken from a record is checked, in every build: after a bounded wait has
-        // run out, phase B can meet records that phase A never wrote.
-        auto load_rec = [&](const uint4 &d, uint32_t r, uint64_t j) -> uint4 {
+        // Record r of a sub-tile as loaded (0s past its end).  Nothing here depends
+        // on the loaded value, so the load of the next sub-tile's records stays in
+        // flight while the current one expands; decode_rec uses it afterwards.
+        auto load_rec = [&](const uint4 &d, uint32_t r) -> uint4 {
             uint4 x = make_uint4(0, 0, 0, 0);
             if (d.y != REC_OVERFLOW && (uint64_t)d.x + d.y <= p.rec_slots && r < d.y) {
                 const uint32_t *rp = p.records + ((size_t)d.x + r) * REC_W;
-                if (BATCH) {
-                    x = __ldcg(reinterpret_cast<const uint4 *>(rp));
-                    x.w = min(x.w, A.n_cum_ids - min(x.z, A.n_cum_ids));
-                } else {
-                    const uint32_t w = __ldcg(rp), t = w >> 10;
-                    x.x = (uint32_t)j * SUB + (w & 1023u) + p.base_off;
-                    if (t < A.n_states) {
-                        const uint2 lc = __ldg(reinterpret_cast<const uint2 *>(A.outl) + t);
-                        x.z = lc.x;
-                        x.w = lc.y;
-                    }
-                }
+                if (BATCH) x = __ldcg(reinterpret_cast<const uint4 *>(rp));
+                else x.x = __ldcg(rp);
             }
             return x;
         };
+        // A loaded record of sub-tile j as (f0, f1, lo, c): the reported offset
+        // (batches: segment, offset in it) and the output list.  Every index taken
+        // from a record is checked, in every build: after a bounded wait has run
+        // out, phase B can meet records that phase A never wrote.  (A record of a
+        // single buffer is never 0: its state is not the initial one.)
+        auto decode_rec = [&](uint4 x, uint64_t j) -> uint4 {
+            if (BATCH) {
+                x.w = min(x.w, A.n_cum_ids - min(x.z, A.n_cum_ids));
+                return x;
+            }
+            uint4 o = make_uint4(0, 0, 0, 0);
+            const uint32_t t = x.x >> 10;
+            if (x.x) {
+                o.x = (uint32_t)j * SUB + (x.x & 1023u) + p.base_off;
+                if (t < A.n_states) {
+                    const uint2 lc = __ldg(reinterpret_cast<const uint2 *>(A.outl) + t);
+                    o.z = lc.x;
+                    o.w = lc.y;
+                }
+            }
+            return o;
+        };
         // (batch mode, with its wider records, keeps the descriptor one sub-tile ahead only: registers)
         uint4 d1 = load_desc(warp), d2 = BATCH ? make_uint4(0, 0, 0, 0) : load_desc(warp + 32);
-        uint4 r1 = load_rec(d1, lane, p0 + warp);
+        uint4 r1 = load_rec(d1, lane);
         for (uint32_t x = warp; x < np; x += 32) {
             const uint64_t j = p0 + x;
             const uint4 dr = d1, rc = r1;
@@ -1081,14 +1135,15 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
                 d1 = d2;
                 d2 = load_desc(x + 64);
             }
-            r1 = load_rec(d1, lane, j + 32);
+            r1 = load_rec(d1, lane);
             unsigned long long o = bases[x];
             if (dr.y != REC_OVERFLOW && (uint64_t)dr.x + dr.y > p.rec_slots) {
                 fail_check(p.hdr, 4, dr.x);
             } else if (dr.y != REC_OVERFLOW) {
-                o += expand(rc.z, rc.w, rc.x, rc.y, o);
+                const uint4 e0 = decode_rec(rc, j);
+                o += expand(e0.z, e0.w, e0.x, e0.y, o);
                 for (uint32_t r0 = 32; r0 < dr.y; r0 += 32) {
-                    const uint4 rr = load_rec(dr, r0 + lane, j);
+                    const uint4 rr = decode_rec(load_rec(dr, r0 + lane), j);
                     o += expand(rr.z, rr.w, rr.x, rr.y, o);
                 }
             } else {
@@ -1109,13 +1164,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const KParams p) {
     }
 }
 
-template <int FILT, bool BATCH, bool ROW16, bool DEEP, uint32_t KSUB>
+template <int FILT, bool BATCH, bool ROW16, bool DEEP, uint32_t KSUB, bool MULTI = false>
 int launch_t(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st) {
     static std::mutex mu;
     static uint32_t set_for[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
-    auto fn = scan_kernel<FILT, BATCH, ROW16, DEEP, KSUB>;
+    auto fn = scan_kernel<FILT, BATCH, ROW16, DEEP, KSUB, MULTI>;
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev >= 0 && dev < 64 && set_for[dev] < smem) {
@@ -1131,10 +1186,14 @@ int launch_t(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st) {
 
 // One cooperative launch of the scan kernel for the automaton's start-filter
 // kind (gram length 0, 4 or 8 bytes), defined in scan_f0.cu / scan_f4.cu /
-// scan_f8.cu.  ksub 2 (62 KiB chunks) is instantiated only without DEEP.
-int launch_f0(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub);
-int launch_f4(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub);
-int launch_f8(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub);
+// scan_f8.cu.  ksub 2 (62 KiB chunks) is instantiated only without DEEP and
+// for one automaton; several automata (multi) only for batches with ksub 1.
+int launch_f0(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub,
+              bool multi);
+int launch_f4(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub,
+              bool multi);
+int launch_f8(KParams &kp, uint32_t smem, uint32_t grid, cudaStream_t st, bool batch, bool r16, bool deep, uint32_t ksub,
+              bool multi);
 
 }  // namespace kern
 }  // namespace glop

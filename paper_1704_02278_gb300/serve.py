@@ -9,10 +9,12 @@ layer: several compiled pattern sets stay resident on the device, requests
 
 * admits a request when its payload, scratch and estimated output fit in a
   device-memory budget (an arena of one allocation, first-fit),
-* batches the admitted requests of one pattern set into a single
-  ``glop_scan_batch`` launch (one segment per request) while earlier batches
-  are still on the GPU -- up to ``max_inflight`` batches overlap, each on its
-  own stream, so copies of one batch run under the scan of another,
+* batches the admitted requests into a single launch (one segment per
+  request) while earlier batches are still on the GPU: requests for several
+  resident sets of one kernel kind share a ``glop_scan_batch_multi`` launch,
+  one group of segments per set, each group scanned with its own automaton --
+  up to ``max_inflight`` batches overlap, each on its own stream, so copies
+  of one batch run under the scan of another,
 * sends a request of at least ``big_bytes`` to a lane of its own: a worker
   thread that scans it end to end through ``glop_scan_host`` (uploads, scans
   and copy-backs of its pieces overlapped) into a pinned result buffer sized
@@ -36,7 +38,10 @@ import time
 
 import numpy as np
 
-from . import Automaton, GlopError, lib, EOVERFLOW, OK
+from . import Automaton, GlopError, lib, EOVERFLOW, OK, batch_multi_kind
+
+MAX_GROUPS = 8   # pattern sets in one batch launch (glop_scan_batch_multi)
+GROUP_ALIGN = 1024  # every set's group of segments starts on this byte boundary
 
 
 @dataclasses.dataclass
@@ -97,8 +102,9 @@ class _Slot:
 
     def __init__(self, torch, device, max_requests: int, out_rows: int):
         self.stream = torch.cuda.Stream(device=device)
-        self.seg_host = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
-        self.first_host = torch.empty(max_requests + 1, dtype=torch.int64, pin_memory=True)
+        # segments: one per request, plus one padding segment per group of a multi-set batch
+        self.seg_host = torch.empty(max_requests + 1 + MAX_GROUPS, dtype=torch.int64, pin_memory=True)
+        self.first_host = torch.empty(max_requests + 1 + MAX_GROUPS, dtype=torch.int64, pin_memory=True)
         self.count_host = torch.empty(1, dtype=torch.int64, pin_memory=True)
         self.out_host = torch.empty((out_rows, 2), dtype=torch.int32, pin_memory=True)
         self.ev = torch.cuda.Event()
@@ -227,6 +233,8 @@ class BatchServer:
         # matches per payload byte per set: a slowly decaying maximum over recent batches (request content
         # varies, and an output bound that is too small costs a second scan)
         self.density = [0.25] * len(self.automata)
+        # sets whose automata share a kernel kind can share one launch
+        self.kind = [batch_multi_kind(a) for a in self.automata]
         self.lib = lib()
         self.stats = {}
         # idle fast path: a lone request of at most fast_bytes while nothing is in flight goes through one
@@ -256,21 +264,42 @@ class BatchServer:
             self.big = None
 
     # -- one batch -------------------------------------------------------------
-    def _cap(self, si: int, nbytes: int) -> int:
-        return int(self.density[si] * nbytes * 1.25) + 4096
+    # A batch is a list of groups (set index, requests of that set in arrival order).  Its text holds the
+    # groups one after another, each starting on a GROUP_ALIGN boundary (the gap before the next group is a
+    # padding segment whose matches nobody reads); one segment per request.
+    def _cap(self, groups) -> int:
+        return int(sum(self.density[si] * sum(r.payload.numel() for r in rs) for si, rs in groups) * 1.25) + 4096
 
-    def _footprint(self, si: int, nbytes: int, nreq: int, cap: int):
+    @staticmethod
+    def _layout(groups):
+        """(text bytes, segment ends, group starts, segment of each request in batch order)."""
+        ends, gstart, rseg = [], [], []
+        pos = 0
+        for gi, (si, rs) in enumerate(groups):
+            gstart.append(pos)
+            for r in rs:
+                pos += r.payload.numel()
+                ends.append(pos)
+                rseg.append(len(ends) - 1)
+            pad = (-pos) % GROUP_ALIGN if gi + 1 < len(groups) else 0
+            if pad:
+                pos += pad
+                ends.append(pos)
+        gstart.append(pos)
+        return pos, ends, gstart, rseg
+
+    def _footprint(self, nbytes: int, nseg: int, cap: int):
         """(workspace bytes, region sizes..., total) of a batch: text, offsets, count, workspace, the
-        (segment, offset, pattern_id) output, the pairs and the per-request runs."""
+        (segment, offset, pattern_id) output, the pairs and the per-segment runs."""
         a = lambda x: (x + 255) // 256 * 256  # noqa: E731
-        ws_bytes = self.automata[si].workspace_bytes(nbytes, nreq)
-        sizes = [a(nbytes), a(8 * (nreq + 1)), 256, a(ws_bytes), a(12 * cap), a(8 * cap), a(8 * (nreq + 1))]
+        ws_bytes = self.automata[0].workspace_bytes(nbytes, nseg)
+        sizes = [a(nbytes), a(8 * (nseg + 1)), 256, a(ws_bytes), a(12 * cap), a(8 * cap), a(8 * (nseg + 1))]
         return ws_bytes, sizes, sum(sizes)
 
-    def _launch(self, reqs, set_index: int, slot: _Slot, cap: int, fp):
+    def _launch(self, groups, slot: _Slot, cap: int, fp):
         torch = self.torch
-        nbytes = sum(r.payload.numel() for r in reqs)
-        nreq = len(reqs)
+        nbytes, ends, gstart, rseg = self._layout(groups)
+        nseg = len(ends)
         ws_bytes, sizes, total = fp
         got = self.arena.alloc(total)
         if got is None:
@@ -281,26 +310,31 @@ class BatchServer:
             offs.append(offs[-1] + z)
         t_off, s_off, c_off, w_off, m_off, p_off, f_off = offs
         b = _Batch()
-        b.reqs, b.set_index, b.slot, b.region, b.nbytes, b.cap = reqs, set_index, slot, (off, ln), nbytes, cap
+        b.groups, b.slot, b.region, b.nbytes, b.cap = groups, slot, (off, ln), nbytes, cap
+        b.reqs = [r for _, rs in groups for r in rs]
+        b.nseg, b.gstart, b.rseg = nseg, np.array(gstart, np.uint64), rseg
         b.offsets = (t_off, s_off, c_off, w_off, m_off, p_off, f_off, ws_bytes)
         seg = slot.seg_host.numpy()
         seg[0] = 0
-        np.cumsum([r.payload.numel() for r in reqs], out=seg[1:nreq + 1])
+        seg[1:nseg + 1] = ends
         st = slot.stream
         with torch.cuda.stream(st):
             text = self.arena.view(t_off, nbytes)
-            a0 = 0
-            for r in reqs:
-                n = r.payload.numel()
-                text[a0:a0 + n].copy_(r.payload, non_blocking=True)
-                a0 += n
-            self.arena.view(s_off, 8 * (nreq + 1)).view(torch.int64).copy_(slot.seg_host[:nreq + 1],
+            for gi, (si, rs) in enumerate(groups):
+                a0 = int(gstart[gi])
+                for r in rs:
+                    n = r.payload.numel()
+                    text[a0:a0 + n].copy_(r.payload, non_blocking=True)
+                    a0 += n
+                if a0 < gstart[gi + 1]:
+                    text[a0:int(gstart[gi + 1])].zero_()
+            self.arena.view(s_off, 8 * (nseg + 1)).view(torch.int64).copy_(slot.seg_host[:nseg + 1],
                                                                            non_blocking=True)
         self._scan_split(b, self.arena.base + m_off, self.arena.base + p_off, cap)
         b.copied = min(cap, slot.out_host.shape[0]) if cap <= self.EAGER_ROWS else 0
         with torch.cuda.stream(st):
             slot.count_host.copy_(self.arena.view(c_off, 8).view(torch.int64), non_blocking=True)
-            slot.first_host[:nreq + 1].copy_(self.arena.view(f_off, 8 * (nreq + 1)).view(torch.int64),
+            slot.first_host[:nseg + 1].copy_(self.arena.view(f_off, 8 * (nseg + 1)).view(torch.int64),
                                              non_blocking=True)
             if b.copied:
                 slot.out_host[:b.copied].copy_(self._pairs_view(b, b.copied), non_blocking=True)
@@ -311,11 +345,18 @@ class BatchServer:
     def _scan_split(self, b, out_ptr: int, pairs_ptr: int, cap: int):
         t_off, s_off, c_off, w_off, m_off, p_off, f_off, ws_bytes = b.offsets
         base, st = self.arena.base, b.slot.stream.cuda_stream
-        rc = self.lib.glop_scan_batch(self.automata[b.set_index].handle, base + t_off, b.nbytes, base + s_off,
-                                      len(b.reqs), out_ptr, cap, base + c_off, base + w_off, ws_bytes, st)
+        if len(b.groups) == 1:
+            rc = self.lib.glop_scan_batch(self.automata[b.groups[0][0]].handle, base + t_off, b.nbytes,
+                                          base + s_off, b.nseg, out_ptr, cap, base + c_off, base + w_off, ws_bytes,
+                                          st)
+        else:
+            hs = (ctypes.c_void_p * len(b.groups))(*[self.automata[si].handle.value for si, _ in b.groups])
+            rc = self.lib.glop_scan_batch_multi(hs, len(b.groups), b.gstart.ctypes.data, base + t_off, b.nbytes,
+                                                base + s_off, b.nseg, out_ptr, cap, base + c_off, base + w_off,
+                                                ws_bytes, st)
         if rc != OK:
             raise GlopError(rc, "glop_scan_batch")
-        rc = self.lib.glop_batch_split(out_ptr, base + c_off, cap, len(b.reqs), pairs_ptr, base + f_off, st)
+        rc = self.lib.glop_batch_split(out_ptr, base + c_off, cap, b.nseg, pairs_ptr, base + f_off, st)
         if rc != OK:
             raise GlopError(rc, "glop_batch_split")
 
@@ -337,9 +378,9 @@ class BatchServer:
                           torch.empty((total, 2), dtype=torch.int32, device=self.device))
             self._scan_split(b, slot.extra[0].data_ptr(), slot.extra[1].data_ptr(), total)
             b.cap, b.copied = total, 0
-            f_off, nreq = b.offsets[6], len(b.reqs)
+            f_off, nseg = b.offsets[6], b.nseg
             with torch.cuda.stream(slot.stream):  # the runs of the full output
-                slot.first_host[:nreq + 1].copy_(self.arena.view(f_off, 8 * (nreq + 1)).view(torch.int64),
+                slot.first_host[:nseg + 1].copy_(self.arena.view(f_off, 8 * (nseg + 1)).view(torch.int64),
                                                  non_blocking=True)
         b.total = total
         if total > b.copied:
@@ -354,30 +395,41 @@ class BatchServer:
     def _finish(self, b, now: float):
         slot = b.slot
         pairs = slot.out_host[:b.total].numpy().view(np.uint32)
-        first = slot.first_host[:len(b.reqs) + 1].numpy()
-        for k, r in enumerate(b.reqs):
+        first = slot.first_host[:b.nseg + 1].numpy()
+        for r, k in zip(b.reqs, b.rseg):
             lo, hi = int(first[k]), int(first[k + 1])
             r.count = hi - lo
             if self.keep:
                 r.matches = pairs[lo:hi].copy()
             r.done = now
-        self.density[b.set_index] = max(0.97 * self.density[b.set_index], b.total / max(b.nbytes, 1))
+        for si, rs in b.groups:
+            nb = sum(r.payload.numel() for r in rs)
+            self.density[si] = max(0.97 * self.density[si], sum(r.count for r in rs) / max(nb, 1))
         slot.extra = None
         self.arena.release(*b.region)
         self.stats["batches"] += 1
         self.stats["requests_per_batch_max"] = max(self.stats["requests_per_batch_max"], len(b.reqs))
+        self.stats["sets_per_batch_max"] = max(self.stats.get("sets_per_batch_max", 0), len(b.groups))
 
-    def _group(self, fifo, si):
-        """Requests of set si from its FIFO, in arrival order, within the batch limits."""
-        group, nbytes = [], 0
-        for r in fifo:
+    def _group(self, order, batched, r0):
+        """The next batch: pending requests in arrival order, from the oldest one on, of every set whose
+        automaton shares r0's kernel kind, within the batch limits; as groups (set, requests), by set."""
+        kind = self.kind[r0.set_index]
+        take, nbytes, by_set = [], 0, {}
+        for r in order:
+            if id(r) in batched or self.kind[r.set_index] != kind:
+                continue
             sz = r.payload.numel()
-            if group and (nbytes + sz > self.max_batch_bytes or len(group) >= self.max_batch_requests
-                          or self._cap(si, nbytes + sz) > self.out_rows):
+            trial = dict(by_set)
+            trial.setdefault(r.set_index, []).append(r)
+            groups = sorted(trial.items())
+            if take and (nbytes + sz > self.max_batch_bytes or len(take) >= self.max_batch_requests
+                         or len(trial) > MAX_GROUPS or self._cap(groups) > self.out_rows):
                 break
-            group.append(r)
+            take.append(r)
+            by_set = trial
             nbytes += sz
-        return group
+        return sorted(by_set.items())
 
     # -- the loop --------------------------------------------------------------
     def serve(self, requests, realtime: bool = True):
@@ -454,29 +506,33 @@ class BatchServer:
                     if rc != EOVERFLOW:
                         raise GlopError(rc, "glop_scan_host")
                     # more matches than the fast path holds: scan it as a batch
-                si = r0.set_index
-                group = self._group(fifos[si], si)
+                groups = self._group(order, batched, r0)
                 while True:
-                    nb = sum(r.payload.numel() for r in group)
-                    cap = self._cap(si, nb)
-                    fp = self._footprint(si, nb, len(group), cap)
-                    if fp[2] <= self.arena.largest_free or len(group) == 1:
+                    nb, ends, _, _ = self._layout(groups)
+                    cap = self._cap(groups)
+                    fp = self._footprint(nb, len(ends), cap)
+                    if fp[2] <= self.arena.largest_free or sum(len(rs) for _, rs in groups) == 1:
                         break
-                    group = group[:(len(group) + 1) // 2]
-                b = self._launch(group, si, free_slots[-1], cap, fp)
+                    # halve the batch: keep the older half of its requests
+                    reqs = sorted((r for _, rs in groups for r in rs), key=lambda r: r.arrival)
+                    keep = set(id(r) for r in reqs[:(len(reqs) + 1) // 2])
+                    groups = [(si, [r for r in rs if id(r) in keep]) for si, rs in groups]
+                    groups = [(si, rs) for si, rs in groups if rs]
+                b = self._launch(groups, free_slots[-1], cap, fp)
                 if b is None and not inflight:
                     # nothing else holds memory: try a minimal output (a larger one is made if needed)
-                    b = self._launch(group, si, free_slots[-1], 4096, self._footprint(si, nb, len(group), 4096))
+                    b = self._launch(groups, free_slots[-1], 4096, self._footprint(nb, len(ends), 4096))
                 if b is None:
                     self.stats["admission_waits"] += 1
                     if not inflight:
                         raise GlopError(2, "request of %d bytes does not fit the HBM budget" %
-                                        group[0].payload.numel())
+                                        groups[0][1][0].payload.numel())
                     break
                 free_slots.pop()
-                for _ in group:
-                    fifos[si].popleft()
-                batched.update(id(r) for r in group)
+                for si, rs in groups:  # (a batch takes the oldest pending requests of each of its sets)
+                    for _ in rs:
+                        fifos[si].popleft()
+                batched.update(id(r) for _, rs in groups for r in rs)
                 inflight.append(b)
                 progressed = True
             if not progressed:
