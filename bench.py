@@ -618,6 +618,13 @@ def dpi_record(dev, steps: int, warmup: int, local: int):
                                 % which},
            "hbm_input_frac": round(N / (ms / 1e3) / 1e9 / hbm, 4),
            "verified": verified["ok"], "verification": verified, "clocks": clk}
+    ins = profiled_value("dpi-2GiB-20000sig", "traffic", "inst_per_launch")
+    if ins is not None:
+        f_sm = (clk or {}).get("sm_mhz") or 2070.0
+        peak_issue = 4 * SMS * f_sm * 1e6
+        rec["issue_roofline"] = {"bound": "issue", "achieved": round(ins / (ms / 1e3) / 1e12, 4),
+                                 "peak": round(peak_issue / 1e12, 4), "unit": "T warp-instructions/s",
+                                 "frac": round(ins / (ms / 1e3) / peak_issue, 4), "inst_per_launch": ins}
     del plan, matches, text, seg, count
     a.close()
     torch.cuda.empty_cache()
