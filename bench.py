@@ -524,10 +524,14 @@ def serve_record(seconds: float, hbm_gib: int, saturated_runs: int = 3):
     # requests of 8 MiB and more go to the large-request lane, sized like the plain server's buffers
     batched = serve.BatchServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4,
                                 max_request_bytes=int(sizes.max()))
-    # warm both (first launches, host allocator)
+    # the same policy with the loop in native code (glop_server_*)
+    native = serve.NativeServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4,
+                                max_request_bytes=int(sizes.max()))
+    # warm all three (first launches, host allocator)
     plain.serve(make()[:20], realtime=False)
     batched.serve(make()[:20], realtime=False)
-    for name, srv in (("plain", plain), ("batched", batched)):
+    native.serve(make()[:20], realtime=False)
+    for name, srv in (("plain", plain), ("batched", batched), ("native", native)):
         reqs = make()
         wall, st = srv.serve(reqs, realtime=True)
         lat = serve.latency_summary(reqs)
@@ -544,7 +548,8 @@ def serve_record(seconds: float, hbm_gib: int, saturated_runs: int = 3):
                          saturated_gbps_best=round(8.0 * out["bytes"] / min(walls) / 1e9, 3),
                          saturated_runs=len(walls), stats=st2, matches=int(sum(r.count for r in reqs2)))
     batched.close()
-    del plain, batched, pools
+    native.close()
+    del plain, batched, native, pools
     torch.cuda.empty_cache()
     return out
 

@@ -446,6 +446,74 @@ glop_status glop_batch_split(const glop_batch_match *d_matches, const uint64_t *
  * Sec. 5).  No scan using h may still be in flight.  NULL is accepted. */
 glop_status glop_destroy(glop_handle h);
 
+/*
+ * glop_server_* -- a scan server's serving loop in native code: several
+ * compiled pattern sets stay resident, requests (a host payload and the set to
+ * scan it with) are admitted into a device-memory budget and batched while
+ * earlier batches are still on the GPU -- the paper's use case (Sec. 1: logs
+ * and rules in, the count and locations of suspect events out) with its
+ * library's overlap of the next batch with the current scan (Sec. 6) and the
+ * real-time operation it leaves for future work (Sec. 8).
+ *
+ * glop_server_create: sets[0 .. n_sets) stay owned by the caller and must
+ * outlive the server; the server allocates hbm_budget bytes of device memory
+ * (payloads, scratch and results of the batches in flight), max_inflight CUDA
+ * streams with pinned buffers, the idle path's staging (fast_bytes) and, when
+ * big_bytes > 0, a large-request lane: a worker thread with device staging for
+ * requests of up to max_request_bytes.  The current device must stay current
+ * for every call.
+ * glop_server_submit: queues request `id` (caller-chosen, unique among
+ * requests not yet released) of `len` bytes at h_payload (host memory; pinned
+ * is fastest), scanned with sets[set].  The payload must stay unchanged until
+ * the request's result is handed out.  Requests of at least big_bytes go to
+ * the lane; the rest wait for a batch.
+ * glop_server_poll: runs the loop -- finished batches advance, a lone request
+ * of at most fast_bytes on an idle server takes one glop_scan_host call, and
+ * pending requests become batches: in arrival order from the oldest, over
+ * every set whose automaton shares the oldest one's kernel kind (one
+ * glop_scan_batch_multi launch), within max_batch_bytes,
+ * max_batch_requests, out_rows_per_batch (the output bound from each set's
+ * matches per byte so far) and the largest free block of the budget.  Stores
+ * up to max_res finished results in res and their number in *n_res; waits up
+ * to wait_us microseconds for one (0: one pass).  A result's matches (count
+ * rows, sorted by offset then pattern id) are pinned host memory owned by the
+ * server until glop_server_release(id).  done_ns is the host's monotonic clock
+ * (CLOCK_MONOTONIC) when the result was complete.  GLOP_ENOMEM when a request
+ * cannot fit the budget even alone; device errors as for the scans.
+ * Not thread-safe: one thread per server (the lane's thread is internal).
+ */
+typedef struct glop_server_s *glop_server; /* opaque */
+typedef struct {
+    uint64_t hbm_budget;         /* device bytes for the batches in flight */
+    uint32_t max_inflight;       /* batches in flight, 1 .. 16 */
+    uint32_t max_batch_requests; /* requests per batch */
+    uint64_t max_batch_bytes;    /* payload bytes per batch */
+    uint64_t out_rows_per_batch; /* largest output bound of a batch, rows (0: max_batch_bytes / 16) */
+    uint64_t fast_bytes;         /* idle path for lone requests up to this size (0: none) */
+    uint64_t big_bytes;          /* requests of at least this size take the lane (0: no lane) */
+    uint64_t max_request_bytes;  /* the largest request the lane must take */
+} glop_server_opts;
+typedef struct {
+    uint64_t id;
+    glop_status status;
+    const glop_match *matches;   /* count rows, pinned, valid until glop_server_release(id) */
+    uint64_t count;
+    uint64_t done_ns;            /* CLOCK_MONOTONIC nanoseconds at completion */
+} glop_server_result;
+typedef struct {
+    uint64_t submitted, batches, fast, big, rescans, admission_waits;
+    uint64_t requests_per_batch_max, sets_per_batch_max;
+    uint64_t pending, inflight;
+} glop_server_stats;
+glop_status glop_server_create(const glop_handle *sets, uint32_t n_sets, const glop_server_opts *opts,
+                               glop_server *out);
+glop_status glop_server_submit(glop_server s, uint64_t id, uint32_t set, const uint8_t *h_payload, uint64_t len);
+glop_status glop_server_poll(glop_server s, glop_server_result *res, uint32_t max_res, uint32_t *n_res,
+                             uint32_t wait_us);
+glop_status glop_server_release(glop_server s, uint64_t id);
+glop_status glop_server_stats_get(glop_server s, glop_server_stats *stats);
+glop_status glop_server_destroy(glop_server s);
+
 /* Static description of a status code. */
 const char *glop_status_str(glop_status s);
 

@@ -39,12 +39,35 @@ SYMBOLS = ["glop_compile", "glop_info_get", "glop_max_pattern_len", "glop_scan_w
            "glop_plan_launch", "glop_plan_destroy", "glop_tune", "glop_batch_split",
            "glop_count_workspace_size", "glop_scan_count", "glop_scan_host_plan", "glop_scan_words",
            "glop_ingest_create", "glop_ingest_feed", "glop_ingest_flush", "glop_ingest_reset", "glop_ingest_info",
-           "glop_ingest_destroy", "glop_scan_batch_multi", "glop_batch_multi_kind"]
+           "glop_ingest_destroy", "glop_scan_batch_multi", "glop_batch_multi_kind", "glop_server_create",
+           "glop_server_submit", "glop_server_poll", "glop_server_release", "glop_server_stats_get",
+           "glop_server_destroy"]
 
 
 class IngestResult(ctypes.Structure):
     """glop_ingest_result: base stream offset, pointer to count (offset, pattern_id) rows, count."""
     _fields_ = [("base", ctypes.c_uint64), ("matches", ctypes.c_void_p), ("count", ctypes.c_uint64)]
+
+
+class ServerOpts(ctypes.Structure):
+    """glop_server_opts."""
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("max_batch_requests", ctypes.c_uint32), ("max_batch_bytes", ctypes.c_uint64),
+                ("out_rows_per_batch", ctypes.c_uint64), ("fast_bytes", ctypes.c_uint64),
+                ("big_bytes", ctypes.c_uint64), ("max_request_bytes", ctypes.c_uint64)]
+
+
+class ServerResult(ctypes.Structure):
+    """glop_server_result: request id, status, pinned (offset, pattern_id) rows, count, completion time."""
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int), ("matches", ctypes.c_void_p),
+                ("count", ctypes.c_uint64), ("done_ns", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    """glop_server_stats."""
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "batches", "fast", "big", "rescans", "admission_waits",
+                                                "requests_per_batch_max", "sets_per_batch_max", "pending",
+                                                "inflight")]
 
 
 class GlopError(RuntimeError):
@@ -105,6 +128,14 @@ def lib():
         L.glop_batch_multi_kind.argtypes = [vp, ctypes.POINTER(u32)]
         L.glop_scan_status.restype = ctypes.c_int
         L.glop_scan_status.argtypes = [vp, vp, ctypes.POINTER(u64)]
+        for name, args in (("glop_server_create", [vp, u32, ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]),
+                           ("glop_server_submit", [vp, u64, u32, vp, u64]),
+                           ("glop_server_poll", [vp, ctypes.POINTER(ServerResult), u32, ctypes.POINTER(u32), u32]),
+                           ("glop_server_release", [vp, u64]),
+                           ("glop_server_stats_get", [vp, ctypes.POINTER(ServerStats)]),
+                           ("glop_server_destroy", [vp])):
+            getattr(L, name).restype = ctypes.c_int
+            getattr(L, name).argtypes = args
         L.glop_scan_host_staging_size.restype = ctypes.c_int
         L.glop_scan_host_staging_size.argtypes = [vp, u64, u64, ctypes.POINTER(u64)]
         L.glop_scan_host.restype = ctypes.c_int

@@ -29,7 +29,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas"
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-Wall", "-I" + INCLUDE, "-I" + CSRC]
 
 CUDA_SOURCES = ["scan.cu", "scan_f0.cu", "scan_f4.cu", "scan_f8.cu", "noalloc.cu", "split.cu", "words.cu"]
-HOST_SOURCES = ["compile.cpp", "api.cpp", "ingest.cpp"]
+HOST_SOURCES = ["compile.cpp", "api.cpp", "ingest.cpp", "server.cpp"]
 HEADERS = ["glop_layout.h", "glop_hash.h", "compile.h", "scan.h", "scan_kernel.cuh"]
 
 

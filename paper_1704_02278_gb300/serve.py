@@ -39,6 +39,7 @@ import time
 import numpy as np
 
 from . import Automaton, GlopError, lib, EOVERFLOW, OK, batch_multi_kind
+from . import ServerOpts as _ServerOpts, ServerResult as _ServerResult, ServerStats as _ServerStats
 
 MAX_GROUPS = 8   # pattern sets in one batch launch (glop_scan_batch_multi)
 GROUP_ALIGN = 1024  # every set's group of segments starts on this byte boundary
@@ -135,7 +136,7 @@ class _BigLane:
         self.torch, self.device, self.automata, self.keep = torch, device, automata, keep
         self.lib = lib()
         self.max_bytes = max_bytes
-        self.stream = torch.cuda.Stream(device=device)
+        self.stream = torch.cuda.Stream(device=device, priority=-1)  # latency first: ahead of batch kernels
         self._size(out_rows)
         self.q = queue.Queue()
         self.completed = 0
@@ -247,7 +248,7 @@ class BatchServer:
                                                  ctypes.byref(need))
             self.fast_staging = torch.empty(int(need.value), dtype=torch.uint8, device=self.device)
             self.fast_out = torch.empty((self.fast_cap, 2), dtype=torch.int32, pin_memory=True)
-            self.fast_stream = torch.cuda.Stream(device=self.device)
+            self.fast_stream = torch.cuda.Stream(device=self.device, priority=-1)
         # the lane for requests of at least big_bytes (0 = none): sized for max_request_bytes, with result rows
         # for two matches per payload byte unless big_out_rows says otherwise
         self.big_bytes = big_bytes if max_request_bytes >= big_bytes > 0 else 0
@@ -545,6 +546,90 @@ class BatchServer:
         if big is not None:
             self.stats["big_rescans"] = big.rescans
         return time.perf_counter() - t0, dict(self.stats)
+
+
+class NativeServer:
+    """The serving loop in native code (``glop_server_*``): the same policy as :class:`BatchServer` -- resident
+    sets, HBM-budget admission, one launch over requests of several sets of a kernel kind, an idle fast path
+    and a large-request lane -- run by the library, with results in pinned memory it pools.  This class only
+    submits requests when they arrive, polls, and copies each result out."""
+
+    def __init__(self, pattern_sets, hbm_budget: int = 8 << 30, max_inflight: int = 4,
+                 max_batch_bytes: int = 256 << 20, max_batch_requests: int = 512, keep_matches: bool = False,
+                 out_rows: int = 0, fast_bytes: int = 1 << 20, big_bytes: int = 8 << 20,
+                 max_request_bytes: int = 0, device=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.automata = [Automaton(p) for p in pattern_sets]
+        self.keep = keep_matches
+        self.lib = lib()
+        o = _ServerOpts(hbm_budget, max_inflight, max_batch_requests, max_batch_bytes, out_rows, fast_bytes,
+                        big_bytes if max_request_bytes >= big_bytes > 0 else 0, max_request_bytes)
+        hs = (ctypes.c_void_p * len(self.automata))(*[a.handle.value for a in self.automata])
+        self._h = ctypes.c_void_p()
+        rc = self.lib.glop_server_create(hs, len(self.automata), ctypes.byref(o), ctypes.byref(self._h))
+        if rc != OK:
+            raise GlopError(rc, "glop_server_create")
+        self._res = (_ServerResult * 256)()
+
+    def close(self):
+        if self._h:
+            self.lib.glop_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        self.lib.glop_server_stats_get(self._h, ctypes.byref(st))
+        return {k: int(getattr(st, k)) for k, _ in _ServerStats._fields_}
+
+    def serve(self, requests, realtime: bool = True):
+        """Serve ``requests`` (sorted by arrival; payloads pinned CPU uint8 tensors).  realtime: each request is
+        submitted at its arrival time; else all at once.  Fills count, matches (when kept) and done (seconds
+        from the start, the library's completion time).  Returns (wall seconds, stats)."""
+        L, h = self.lib, self._h
+        n = len(requests)
+        by_id = {}
+        nres = ctypes.c_uint32()
+        t0 = time.perf_counter()
+        t0_ns = time.monotonic_ns()
+        nxt = done = 0
+        before = self.stats()
+        while done < n:
+            now = time.perf_counter() - t0
+            while nxt < n and (not realtime or requests[nxt].arrival <= now):
+                r = requests[nxt]
+                by_id[nxt] = r
+                rc = L.glop_server_submit(h, nxt, r.set_index, r.payload.data_ptr() if r.payload.numel() else None,
+                                          r.payload.numel())
+                if rc != OK:
+                    raise GlopError(rc, "glop_server_submit")
+                nxt += 1
+            wait = 0 if (realtime and nxt < n) else 200
+            rc = L.glop_server_poll(h, self._res, len(self._res), ctypes.byref(nres), wait)
+            if rc != OK:
+                raise GlopError(rc, "glop_server_poll")
+            for k in range(nres.value):
+                res = self._res[k]
+                r = by_id.pop(res.id)
+                if res.status != OK:
+                    raise GlopError(res.status, "request %d" % r.rid)
+                r.count = int(res.count)
+                if self.keep:
+                    r.matches = (np.ctypeslib.as_array(ctypes.cast(res.matches, ctypes.POINTER(ctypes.c_uint32)),
+                                                       shape=(2 * r.count,)).reshape(-1, 2).copy()
+                                 if r.count else np.zeros((0, 2), np.uint32))
+                r.done = (res.done_ns - t0_ns) / 1e9
+                L.glop_server_release(h, res.id)
+                done += 1
+            if not nres.value and realtime and nxt < n:
+                time.sleep(max(0.0, min(requests[nxt].arrival - (time.perf_counter() - t0), 0.0002)))
+        wall = time.perf_counter() - t0
+        after = self.stats()
+        st = {k: after[k] - before[k] for k in ("batches", "fast", "big", "rescans", "admission_waits")}
+        st["requests_per_batch_max"] = after["requests_per_batch_max"]
+        st["sets_per_batch_max"] = after["sets_per_batch_max"]
+        return wall, st
 
 
 class PlainServer:

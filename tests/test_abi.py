@@ -104,3 +104,19 @@ def test_new_entry_points_reject_bad_arguments_before_any_device_work(libpath):
     assert lib.glop_ingest_reset(None) == glop.EINVAL
     assert lib.glop_ingest_info(None, None, None) == glop.EINVAL
     assert lib.glop_ingest_destroy(None) == glop.EINVAL
+    # several automata in one batch: no handles, too many groups
+    assert lib.glop_scan_batch_multi(None, 1, p, None, 0, p, 0, None, 0, p, p, 0, None) == glop.EINVAL
+    assert lib.glop_scan_batch_multi(p, 9, p, None, 0, p, 0, None, 0, p, p, 0, None) == glop.EINVAL
+    assert lib.glop_batch_multi_kind(None, None) == glop.EINVAL
+    # the native server: NULL sets, options or object; bad options
+    srv = ctypes.c_void_p()
+    opts = glop.ServerOpts(1 << 20, 2, 16, 1 << 20, 0, 0, 0, 0)
+    assert lib.glop_server_create(None, 1, ctypes.byref(opts), ctypes.byref(srv)) == glop.EINVAL and not srv.value
+    assert lib.glop_server_create(p, 0, ctypes.byref(opts), ctypes.byref(srv)) == glop.EINVAL
+    bad = glop.ServerOpts(1 << 20, 0, 16, 1 << 20, 0, 0, 0, 0)  # no stream slots
+    assert lib.glop_server_create(p, 1, ctypes.byref(bad), ctypes.byref(srv)) == glop.EINVAL
+    assert lib.glop_server_submit(None, 0, 0, None, 0) == glop.EINVAL
+    assert lib.glop_server_poll(None, None, 0, ctypes.byref(n), 0) == glop.EINVAL
+    assert lib.glop_server_release(None, 0) == glop.EINVAL
+    assert lib.glop_server_stats_get(None, None) == glop.EINVAL
+    assert lib.glop_server_destroy(None) == glop.OK
