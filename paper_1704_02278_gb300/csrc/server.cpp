@@ -145,6 +145,13 @@ struct PinnedPool {
     }
 };
 
+// A batch's result rows: one pinned block holding every request's rows, given back to the pool when the
+// last of its requests is released.
+struct Block {
+    void *p = nullptr;
+    uint32_t refs = 0;
+};
+
 struct Request {
     uint64_t id;
     uint32_t set;
@@ -153,7 +160,8 @@ struct Request {
     // results
     glop_status st = GLOP_OK;
     uint64_t count = 0;
-    glop_match *rows = nullptr;  // pinned, from the pool
+    glop_match *rows = nullptr;  // pinned: inside blk, or a block of its own from the pool (or the lane's rows)
+    Block *blk = nullptr;
     uint64_t done_ns = 0;
 };
 
@@ -371,21 +379,33 @@ glop_status advance(glop_server_s *S, Batch &b) {
     b.total = total;
     const glop_match *dpairs =
         reinterpret_cast<const glop_match *>(b.extra_pairs ? b.extra_pairs : (void *)(S->arena.base + b.p_off));
+    // every request's rows in one pinned block, copied back in one piece (or from the eager rows)
+    Block *blk = new (std::nothrow) Block();
+    if (!blk) return GLOP_ENOMEM;
+    blk->p = S->pool.get(8 * (total + 1));
+    if (!blk->p) {
+        delete blk;
+        return GLOP_ENOMEM;
+    }
+    glop_match *rows = reinterpret_cast<glop_match *>(blk->p);
+    if (total) {
+        if (b.eager) std::memcpy(rows, sl.eager, 8 * total);
+        else if (cudaMemcpyAsync(rows, dpairs, 8 * total, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GLOP_ECUDA;
+    }
     size_t k = 0;
     for (auto &g : b.groups) {
         for (Request *r : g.second) {
             const uint32_t si = b.rseg[k++];
             const uint64_t lo = sl.first_host[si], hi = sl.first_host[si + 1];
             r->count = hi - lo;
-            r->rows = reinterpret_cast<glop_match *>(S->pool.get(8 * (r->count + 1)));
-            if (!r->rows) return GLOP_ENOMEM;
-            if (!r->count) continue;
-            if (b.eager) {
-                std::memcpy(r->rows, sl.eager + lo, 8 * r->count);
-            } else if (cudaMemcpyAsync(r->rows, dpairs + lo, 8 * r->count, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
-                return GLOP_ECUDA;
-            }
+            r->rows = rows + lo;
+            r->blk = blk;
+            ++blk->refs;
         }
+    }
+    if (!blk->refs) {
+        S->pool.put(blk->p);
+        delete blk;
     }
     if (cudaEventRecord(sl.ev, st) != cudaSuccess) return GLOP_ECUDA;
     b.stage = 2;
@@ -469,12 +489,23 @@ void lane_main(glop_server_s *S) {
             r = S->lane_q.front();
             S->lane_q.pop_front();
         }
-        // results into the lane's pinned rows (two rows per payload byte, sized at creation), or, while a
-        // caller still holds the previous lane result, into a block of the pool; one rescan into exact rows
-        // when a request has more matches than that
+        // results into the lane's pinned rows (two rows per payload byte, sized at creation); while a caller
+        // still holds the previous lane result, into a block of the pool sized from the set's matches per
+        // byte so far; one rescan into exact rows when a request has more matches than its rows
+        double dens;
+        {
+            std::lock_guard<std::mutex> lk(S->fin_mu);
+            dens = S->density[r->set];
+        }
         uint64_t cap = S->lane_rows;
         glop_match *rows = nullptr;
-        if (!S->lane_buf_busy.exchange(true)) rows = S->lane_buf;
+        // (a caller that polls hands the previous lane result back within microseconds: wait up to 20 ms for
+        // it rather than make a large pinned block, which can take longer than the scan)
+        bool got = false;
+        const uint64_t t_wait = now_ns() + 20000000ull;
+        while (!(got = !S->lane_buf_busy.exchange(true)) && now_ns() < t_wait) std::this_thread::yield();
+        if (got) rows = S->lane_buf;
+        else cap = std::min<uint64_t>(S->lane_rows, (uint64_t)(2.5 * dens * (double)r->len) + 65536);
         while (true) {
             uint64_t need = 0;
             glop_scan_host_staging_size(S->sets[r->set], r->len, cap, &need);
@@ -511,6 +542,10 @@ void lane_main(glop_server_s *S) {
             break;
         }
         r->rows = rows;
+        if (r->st == GLOP_OK) {
+            std::lock_guard<std::mutex> lk(S->fin_mu);
+            S->density[r->set] = std::max(0.97 * S->density[r->set], (double)r->count / (double)std::max<uint64_t>(r->len, 1));
+        }
         r->done_ns = now_ns();
         std::lock_guard<std::mutex> lk(S->fin_mu);
         S->finished.push_back(r);
@@ -565,6 +600,8 @@ glop_status glop_server_create(const glop_handle *sets, uint32_t n_sets, const g
         std::vector<void *> warm;
         for (uint64_t sz = 1 << 16; sz <= (16ull << 20); sz <<= 2)
             for (uint32_t k = 0; k < 4 * S->o.max_inflight; ++k) warm.push_back(S->pool.get(sz));
+        for (uint64_t sz = 64ull << 20; sz <= (256ull << 20); sz <<= 2)
+            for (uint32_t k = 0; k < S->o.max_inflight; ++k) warm.push_back(S->pool.get(sz));
         for (void *p : warm) {
             if (!p) return fail(GLOP_ENOMEM);
             S->pool.put(p);
@@ -745,8 +782,17 @@ glop_status glop_server_release(glop_server S, uint64_t id) {
     if (!S) return GLOP_EINVAL;
     auto it = S->handed.find(id);
     if (it == S->handed.end()) return GLOP_EINVAL;
-    if (it->second->rows && it->second->rows == S->lane_buf) S->lane_buf_busy = false;
-    else S->pool.put(it->second->rows);
+    Request *r = it->second;
+    if (r->blk) {
+        if (--r->blk->refs == 0) {
+            S->pool.put(r->blk->p);
+            delete r->blk;
+        }
+    } else if (r->rows && r->rows == S->lane_buf) {
+        S->lane_buf_busy = false;
+    } else {
+        S->pool.put(r->rows);
+    }
     delete it->second;
     S->handed.erase(it);
     return GLOP_OK;
@@ -773,16 +819,22 @@ glop_status glop_server_destroy(glop_server S) {
     for (Slot &sl : S->slots)
         if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (S->lane_stream) cudaStreamSynchronize(S->lane_stream);
+    std::vector<Block *> blocks;  // (shared by several requests: deleted once)
+    auto drop = [&](Request *r) {
+        if (r->blk && std::find(blocks.begin(), blocks.end(), r->blk) == blocks.end()) blocks.push_back(r->blk);
+        delete r;
+    };
     for (Batch *b : S->inflight) {
         if (!b->extra_len && b->extra_out) cudaFree(b->extra_out);
         if (!b->extra_len && b->extra_pairs) cudaFree(b->extra_pairs);
         for (auto &g : b->groups)
-            for (Request *r : g.second) delete r;
+            for (Request *r : g.second) drop(r);
         delete b;
     }
-    for (Request *r : S->pending) delete r;
-    for (Request *r : S->finished) delete r;
-    for (auto &kv : S->handed) delete kv.second;
+    for (Request *r : S->pending) drop(r);
+    for (Request *r : S->finished) drop(r);
+    for (auto &kv : S->handed) drop(kv.second);
+    for (Block *b : blocks) delete b;
     for (Slot &sl : S->slots) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.ev) cudaEventDestroy(sl.ev);
