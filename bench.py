@@ -522,11 +522,13 @@ def serve_record(seconds: float, hbm_gib: int, saturated_runs: int = 3):
     plain = serve.PlainServer(sets, max_request_bytes=int(sizes.max()))
     # pinned result buffers sized for a full 256 MiB batch at up to 0.25 matches per byte
     # requests of 8 MiB and more go to the large-request lane, sized like the plain server's buffers
+    # (a lone request of up to 8 MiB on an idle server takes one end-to-end call, as the plain loop does;
+    # larger ones take the lane)
     batched = serve.BatchServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4,
-                                max_request_bytes=int(sizes.max()))
+                                max_request_bytes=int(sizes.max()), fast_bytes=8 << 20)
     # the same policy with the loop in native code (glop_server_*)
     native = serve.NativeServer(sets, hbm_budget=hbm_gib << 30, out_rows=(256 << 20) // 4,
-                                max_request_bytes=int(sizes.max()))
+                                max_request_bytes=int(sizes.max()), fast_bytes=8 << 20)
     # warm all three (first launches, host allocator)
     plain.serve(make()[:20], realtime=False)
     batched.serve(make()[:20], realtime=False)

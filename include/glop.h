@@ -504,6 +504,7 @@ typedef struct {
     uint64_t submitted, batches, fast, big, rescans, admission_waits;
     uint64_t requests_per_batch_max, sets_per_batch_max;
     uint64_t pending, inflight;
+    uint64_t pinned_allocs;  /* pinned result blocks made after creation (the pool had none of the size) */
 } glop_server_stats;
 glop_status glop_server_create(const glop_handle *sets, uint32_t n_sets, const glop_server_opts *opts,
                                glop_server *out);

@@ -67,7 +67,7 @@ class ServerStats(ctypes.Structure):
     """glop_server_stats."""
     _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "batches", "fast", "big", "rescans", "admission_waits",
                                                 "requests_per_batch_max", "sets_per_batch_max", "pending",
-                                                "inflight")]
+                                                "inflight", "pinned_allocs")]
 
 
 class GlopError(RuntimeError):

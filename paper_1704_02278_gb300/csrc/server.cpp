@@ -111,6 +111,7 @@ struct PinnedPool {
     std::mutex mu;
     std::multimap<uint64_t, void *> idle;  // capacity (bytes) -> block
     std::map<void *, uint64_t> cap;
+    std::atomic<uint64_t> allocs{0};  // blocks made (cudaHostAlloc calls)
     void *get(uint64_t bytes) {
         bytes = std::max<uint64_t>(bytes, 1 << 16);
         {
@@ -122,9 +123,13 @@ struct PinnedPool {
                 return p;
             }
         }
+        // powers of two up to 64 MiB, then multiples of 64 MiB (a batch's block of a few hundred MiB would
+        // otherwise take up to twice its size)
         uint64_t c = 1 << 16;
-        while (c < bytes) c <<= 1;
+        while (c < bytes && c < (64ull << 20)) c <<= 1;
+        if (c < bytes) c = (bytes + (64ull << 20) - 1) & ~((64ull << 20) - 1);
         void *p = nullptr;
+        ++allocs;
         if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
@@ -228,6 +233,7 @@ struct glop_server_s {
     cudaStream_t lane_stream = nullptr;
     std::atomic<uint64_t> lane_active{0};
     glop_server_stats stats{};
+    uint64_t warm_allocs = 0;  // pool blocks made at creation
 };
 
 namespace {
@@ -594,18 +600,24 @@ glop_status glop_server_create(const glop_handle *sets, uint32_t n_sets, const g
             return fail(GLOP_ENOMEM);
         S->free_slots.push_back(&sl);
     }
-    // result blocks made ahead of time (a pinned allocation in the loop would stall it): for every stream
-    // slot, blocks of 64 KiB to 16 MiB
+    // result blocks made ahead of time (a pinned allocation in the loop stalls it for as long as the
+    // allocation takes, ~0.1 s for a few hundred MiB): for every stream slot, blocks of 64 KiB to 16 MiB,
+    // of 64 and 256 MiB, and of the largest batch's rows (one more of those than there are slots, for the
+    // block whose requests the caller has not released yet)
     {
         std::vector<void *> warm;
         for (uint64_t sz = 1 << 16; sz <= (16ull << 20); sz <<= 2)
             for (uint32_t k = 0; k < 4 * S->o.max_inflight; ++k) warm.push_back(S->pool.get(sz));
         for (uint64_t sz = 64ull << 20; sz <= (256ull << 20); sz <<= 2)
             for (uint32_t k = 0; k < S->o.max_inflight; ++k) warm.push_back(S->pool.get(sz));
+        const uint64_t top = 8 * (S->o.out_rows_per_batch + 1);
+        if (top > (256ull << 20))
+            for (uint32_t k = 0; k <= S->o.max_inflight; ++k) warm.push_back(S->pool.get(top));
         for (void *p : warm) {
             if (!p) return fail(GLOP_ENOMEM);
             S->pool.put(p);
         }
+        S->warm_allocs = S->pool.allocs;
     }
     // latency first: the idle path and the lane run on the device's highest-priority streams, so their
     // kernels are scheduled ahead of a batch's when both wait for the SMs
@@ -668,7 +680,9 @@ glop_status glop_server_poll(glop_server S, glop_server_result *res, uint32_t ma
     if (!S || !n_res || (max_res && !res)) return GLOP_EINVAL;
     *n_res = 0;
     const uint64_t t_end = now_ns() + 1000ull * wait_us;
+    uint32_t idle = 0;  // loop iterations since the last completion or launch
     while (true) {
+        const size_t n_inflight = S->inflight.size(), n_pending = S->pending.size();
         // completions
         for (size_t i = 0; i < S->inflight.size();) {
             Batch *b = S->inflight[i];
@@ -678,6 +692,7 @@ glop_status glop_server_poll(glop_server S, glop_server_result *res, uint32_t ma
                 continue;
             }
             if (q != cudaSuccess) return GLOP_ECUDA;
+            idle = 0;
             if (b->stage == 1) {
                 const glop_status rc = advance(S, *b);
                 if (rc != GLOP_OK) return rc;
@@ -691,22 +706,43 @@ glop_status glop_server_poll(glop_server S, glop_server_result *res, uint32_t ma
         while (!S->pending.empty() && !S->free_slots.empty()) {
             Request *r0 = S->pending.front();
             if (S->inflight.empty() && S->pending.size() == 1 && S->o.fast_bytes && r0->len <= S->o.fast_bytes) {
-                r0->rows = reinterpret_cast<glop_match *>(S->pool.get(8 * (S->fast_cap + 1)));
-                if (!r0->rows) return GLOP_ENOMEM;
+                // rows for this request from the set's matches per byte so far (a block sized for the
+                // largest fast request would drain the pool's large blocks and make new ones in the loop);
+                // more matches than that: once more with the exact count, while it fits the fast path
+                double dens;
+                {
+                    std::lock_guard<std::mutex> lk(S->fin_mu);
+                    dens = S->density[r0->set];
+                }
+                uint64_t fcap = std::min<uint64_t>(S->fast_cap, (uint64_t)(2.5 * dens * (double)r0->len) + 65536);
+                glop_status rc = GLOP_EOVERFLOW;
                 uint64_t cnt = 0;
-                const glop_status rc = glop_scan_host(S->sets[r0->set], r0->payload, r0->len, r0->rows, S->fast_cap,
-                                                      &cnt, S->fast_staging, S->fast_staging_bytes, S->fast_stream);
+                for (int pass = 0; pass < 2 && rc == GLOP_EOVERFLOW; ++pass) {
+                    if (pass) {
+                        if (cnt > S->fast_cap) break;
+                        fcap = cnt;
+                        ++S->stats.rescans;
+                    }
+                    r0->rows = reinterpret_cast<glop_match *>(S->pool.get(8 * (fcap + 1)));
+                    if (!r0->rows) return GLOP_ENOMEM;
+                    rc = glop_scan_host(S->sets[r0->set], r0->payload, r0->len, r0->rows, fcap, &cnt, S->fast_staging,
+                                        S->fast_staging_bytes, S->fast_stream);
+                    if (rc != GLOP_OK) {
+                        S->pool.put(r0->rows);
+                        r0->rows = nullptr;
+                    }
+                }
                 if (rc == GLOP_OK) {
                     r0->count = cnt;
                     r0->done_ns = now_ns();
                     S->pending.pop_front();
                     ++S->stats.fast;
                     std::lock_guard<std::mutex> lk(S->fin_mu);
+                    if (r0->len >= (1u << 20))  // (a small request's density says little about the set's)
+                        S->density[r0->set] = std::max(0.97 * S->density[r0->set], (double)cnt / (double)r0->len);
                     S->finished.push_back(r0);
                     continue;
                 }
-                S->pool.put(r0->rows);
-                r0->rows = nullptr;
                 if (rc != GLOP_EOVERFLOW) return rc;
                 // more matches than the fast path holds: scan it as a batch
             }
@@ -773,7 +809,11 @@ glop_status glop_server_poll(glop_server S, glop_server_result *res, uint32_t ma
         }
         if (*n_res || now_ns() >= t_end) break;
         if (S->inflight.empty() && S->pending.empty() && !S->lane_active) break;
-        std::this_thread::yield();
+        // Waiting: a tight loop of event queries contends with the lane's thread for the driver (its copies
+        // and launches are many short calls), so after a few idle turns the loop sleeps between queries.
+        if (S->inflight.size() != n_inflight || S->pending.size() != n_pending) idle = 0;
+        if (++idle > 16) std::this_thread::sleep_for(std::chrono::microseconds(10));
+        else std::this_thread::yield();
     }
     return GLOP_OK;
 }
@@ -803,6 +843,7 @@ glop_status glop_server_stats_get(glop_server S, glop_server_stats *st) {
     *st = S->stats;
     st->pending = S->pending.size();
     st->inflight = S->inflight.size();
+    st->pinned_allocs = S->pool.allocs - S->warm_allocs;
     return GLOP_OK;
 }
 

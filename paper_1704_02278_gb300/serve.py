@@ -605,7 +605,10 @@ class NativeServer:
                 if rc != OK:
                     raise GlopError(rc, "glop_server_submit")
                 nxt += 1
-            wait = 0 if (realtime and nxt < n) else 200
+            if realtime and nxt < n:  # the library waits (and keeps the loop moving) until the next arrival
+                wait = int(max(0.0, min(requests[nxt].arrival - (time.perf_counter() - t0), 2e-4)) * 1e6)
+            else:
+                wait = 200
             rc = L.glop_server_poll(h, self._res, len(self._res), ctypes.byref(nres), wait)
             if rc != OK:
                 raise GlopError(rc, "glop_server_poll")
@@ -622,11 +625,10 @@ class NativeServer:
                 r.done = (res.done_ns - t0_ns) / 1e9
                 L.glop_server_release(h, res.id)
                 done += 1
-            if not nres.value and realtime and nxt < n:
-                time.sleep(max(0.0, min(requests[nxt].arrival - (time.perf_counter() - t0), 0.0002)))
         wall = time.perf_counter() - t0
         after = self.stats()
-        st = {k: after[k] - before[k] for k in ("batches", "fast", "big", "rescans", "admission_waits")}
+        st = {k: after[k] - before[k] for k in ("batches", "fast", "big", "rescans", "admission_waits",
+                                                 "pinned_allocs")}
         st["requests_per_batch_max"] = after["requests_per_batch_max"]
         st["sets_per_batch_max"] = after["sets_per_batch_max"]
         return wall, st

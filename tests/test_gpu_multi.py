@@ -126,3 +126,31 @@ def test_multi_rejects_bad_groups():
     assert call([a[0], a[0]], [0, 2048, 4096]) == glop.OK
     st = L.glop_scan_status(ws.data_ptr(), torch.cuda.current_stream().cuda_stream, None)
     assert st == glop.EINVAL and int(cnt.item()) == 0
+
+
+def test_multi_short_and_deep_patterns():
+    """Several automata of the other kernel kinds in one launch: no start filter (patterns of 1-3 bytes),
+    and patterns longer than the staged halo (walks that read past the chunk's staged bytes)."""
+    rng = np.random.default_rng(7)
+    alpha = np.frombuffer(b"abcd", np.uint8)
+
+    def text(n):
+        return alpha[rng.integers(0, 4, n)].copy()
+
+    # no start filter: every set has a pattern shorter than 4 bytes
+    short = [W.Patterns.from_list([b"a", b"ab", b"abc", b"dcb", b"abcdabcd"]),
+             W.Patterns.from_list([b"b", b"cc", b"dab", b"acbd"])]
+    autos = [glop.Automaton(p) for p in short]
+    assert glop.batch_multi_kind(autos[0]) == glop.batch_multi_kind(autos[1])
+    _run(short, [[text(5000), text(1), text(70000)], [text(31 * 1024), text(3)]], autos)
+    # deep: one pattern of 1,500 bytes (longer than the 1 KiB halo) in each set, planted in the payloads
+    long_a = text(1500).tobytes()
+    long_b = text(1300).tobytes()
+    deep = [W.Patterns.from_list([long_a, long_a[:700], b"abca"]), W.Patterns.from_list([long_b, b"dddd", b"cabd"])]
+    pa = text(100000)
+    pa[31 * 1024 - 600:31 * 1024 - 600 + 1500] = np.frombuffer(long_a, np.uint8)  # across a chunk boundary
+    pb = text(70000)
+    pb[5000:6300] = np.frombuffer(long_b, np.uint8)
+    autos = [glop.Automaton(p) for p in deep]
+    assert glop.batch_multi_kind(autos[0]) == glop.batch_multi_kind(autos[1])
+    _run(deep, [[pa, text(2000)], [pb]], autos)
