@@ -341,12 +341,12 @@ __device__ __forceinline__ bool step(const GlopDevAutomaton &A, const uint8_t *c
         const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf) + (pos >> 2);
         const uint32_t sh = 8 * (pos & 3);
         const uint32_t y0 = b32[0], y1 = b32[1], y2 = b32[2], y3 = b32[3], y4 = b32[4];
-        const unsigned long long x01 = ((unsigned long long)(__funnelshift_r(y1, y2, sh) ^ c0.y) << 32) |
-                                       (__funnelshift_r(y0, y1, sh) ^ c0.x);
-        const unsigned long long x23 = ((unsigned long long)(__funnelshift_r(y3, y4, sh) ^ c0.w) << 32) |
-                                       (__funnelshift_r(y2, y3, sh) ^ c0.z);
-        m = x01 ? (uint32_t)(__ffsll((long long)x01) - 1) >> 3
-                : x23 ? 8 + ((uint32_t)(__ffsll((long long)x23) - 1) >> 3) : 16u;
+        // the first differing 32-bit word, then its first differing byte
+        uint32_t dw = __funnelshift_r(y0, y1, sh) ^ c0.x, mb = 0;
+        if (!dw) { dw = __funnelshift_r(y1, y2, sh) ^ c0.y; mb = 4; }
+        if (!dw) { dw = __funnelshift_r(y2, y3, sh) ^ c0.z; mb = 8; }
+        if (!dw) { dw = __funnelshift_r(y3, y4, sh) ^ c0.w; mb = 12; }
+        m = dw ? mb + ((uint32_t)__clz(__brev(dw)) >> 3) : 16u;
         m = min(m, lim);
     } else {
         m = 0;
@@ -465,6 +465,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
     // store no records and phase B walks every sub-tile again).  Batches:
     // (segment, offset in the segment, output-list start, count).
     constexpr uint32_t REC_W = BATCH ? 4u : 1u;  // record size in uint32
+    // every output list shorter than 2^22 entries: a sub-tile's match count (at most 1,024 lists) fits 32 bits
+    const bool narrow = A.n_cum_ids < (1u << 22);
 
     // Start of the walk from sub-tile offset off (walk bound endr): the state
     // reached by the first gram_len bytes, | GLOP_TERM when it is terminal;
@@ -597,18 +599,36 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
     // number of outputs.
     auto expand = [&](uint32_t lo, uint32_t c, uint32_t f0, uint32_t f1, unsigned long long o) -> uint32_t {
         const uint32_t incl = warp_incl_scan(c, lane), excl = incl - c, tot = __shfl_sync(FULL, incl, 31);
+        if (!tot) return 0u;
+        // output slot s of the lane that owns it reads list entry base + s
+        const uint32_t base = lo - excl;
+        // When the lanes with outputs are a prefix of the warp (records fill lanes 0, 1, ...), the owner of
+        // slot i is the number of lanes that start at or before i, less one: the lanes that started in
+        // earlier rounds plus the starts at or below this lane's slot in a mask of this round's starts.
+        const uint32_t nz = __ballot_sync(FULL, c != 0u);
+        const bool prefix = (nz & (nz + 1u)) == 0u;
+        const uint32_t le = (2u << lane) - 1u;
+        const uint32_t room = o < p.cap ? (uint32_t)min(p.cap - o, (unsigned long long)tot) : 0u;
+        uint32_t before = 0;
         for (uint32_t s0 = 0; s0 < tot; s0 += 32) {
             const uint32_t slot = s0 + lane;
-            const uint32_t ow = owner_of(excl, slot);
-            const uint32_t lo_o = __shfl_sync(FULL, lo, ow), ex_o = __shfl_sync(FULL, excl, ow);
-            const uint32_t f0_o = __shfl_sync(FULL, f0, ow), f1_o = __shfl_sync(FULL, f1, ow);
-            const unsigned long long pos = o + slot;
-            if (slot < tot && pos < p.cap) {
+            uint32_t ow;
+            if (prefix) {
+                const uint32_t starts = __reduce_or_sync(FULL, (c && excl - s0 < 32u) ? 1u << (excl - s0) : 0u);
+                ow = before + __popc(starts & le) - 1u;
+                before += __popc(starts);
+            } else {
+                ow = owner_of(excl, slot);
+            }
+            const uint32_t base_o = __shfl_sync(FULL, base, ow), f0_o = __shfl_sync(FULL, f0, ow);
+            const uint32_t f1_o = BATCH ? __shfl_sync(FULL, f1, ow) : 0u;
+            if (slot < room) {
                 uint32_t pid = 0;
-                const uint32_t q = lo_o + (slot - ex_o);
+                const uint32_t q = base_o + slot;
+                const unsigned long long pos = o + slot;
                 // (lo + c never passes the end of cum_ids: walks end at valid states, and
                 // load_rec bounds what it takes from records)
-                GLOP_CK(p.hdr, q < A.n_cum_ids, 25, lo_o) pid = q < n_ids_s ? ids_s[q] : __ldg(A.cum_ids + q);
+                GLOP_CK(p.hdr, q < A.n_cum_ids, 25, base_o) pid = q < n_ids_s ? ids_s[q] : __ldg(A.cum_ids + q);
                 if (BATCH) {
                     uint32_t *ob = reinterpret_cast<uint32_t *>(p.out) + 3 * pos;
                     __stcs(ob, f0_o);
@@ -688,12 +708,21 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
         }
         const uint32_t rabs = blockIdx.x * p.rec_cap_cta + rbase;
         uint32_t *recs = p.records + (size_t)rabs * REC_W;
-        uint32_t nrec = 0;
-        unsigned long long nmatch = 0, o = obase;
+        uint32_t nrec = 0, nm32 = 0;
+        unsigned long long nm64 = 0, o = obase;
         for (uint32_t b0 = 0; b0 < total; b0 += QCAP) {
             const uint32_t nb = min(QCAP, total - b0);
             // (1) survivor offsets
-            if (excl < b0 + nb && excl + n > b0) {
+            if (total <= QCAP) {
+                // all of them fit (the usual case): each lane writes its own from the highest
+                uint32_t m = mask;
+                uint16_t *qp = qoff + excl + n;
+                while (m) {
+                    const uint32_t bit = 31u - __clz(m);
+                    m ^= 1u << bit;
+                    *--qp = (uint16_t)(32 * lane + bit);
+                }
+            } else if (excl < b0 + nb && excl + n > b0) {
                 uint32_t m = mask, idx = excl;
                 while (m) {
                     const uint32_t bit = __ffs(m) - 1;
@@ -849,7 +878,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
                     const uint32_t b = __ballot_sync(FULL, t != 0);
                     if (t) {
                         const uint32_t q = nrec + __popc(b & lt);
-                        nmatch += c;
+                        if (narrow) nm32 += c;
+                        else nm64 += c;
                         GLOP_CK(p.hdr, ovf || (uint64_t)rabs + q < p.rec_slots, 27, rabs + q)
                         if (!ovf) {
                             uint32_t *rp = recs + (size_t)q * REC_W;
@@ -863,7 +893,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
             __syncwarp();
         }
         if (!direct && !p.state_hits) {
-            nmatch = warp_sum64(nmatch);
+            const unsigned long long nmatch = narrow ? (unsigned long long)__reduce_add_sync(FULL, nm32) : warp_sum64(nm64);
             if (lane == 0) {
                 SubDesc d;
                 d.rec_start = rabs;

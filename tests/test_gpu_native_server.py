@@ -94,3 +94,26 @@ def test_native_server_empty_tiny_and_tight_budget():
         assert srv.stats()["admission_waits"] > 0
     finally:
         srv.close()
+
+
+def test_native_server_idle_path_rows_and_retries():
+    """Lone requests on an idle server with more matches per byte than the server has seen so far: the idle
+    path's rows (sized from the set's density so far) overflow, and the request is scanned again with the exact
+    count while that fits the idle path, else as a batch; every result still equals the oracle's."""
+    sets = [W.Patterns.from_list([b"a", b"aa"]), W.Patterns.from_list([b"ab", b"abab", b"b"])]
+    a = np.full(1 << 20, ord("a"), np.uint8)
+    ab = np.frombuffer(b"ab" * (1 << 17), np.uint8)
+    payloads = [(0, a[:256 << 10]), (1, ab[:100000]), (0, a[:900 << 10]), (0, a[:256 << 10]), (1, ab[:3])]
+    reqs = [serve.Request(i, si, torch.from_numpy(p.copy()).pin_memory(), 0.05 * i)
+            for i, (si, p) in enumerate(payloads)]
+    exp = _expected(sets, reqs)
+    srv = serve.NativeServer(sets, hbm_budget=1 << 30, keep_matches=True, fast_bytes=1 << 20, big_bytes=0)
+    try:
+        wall, st = srv.serve(reqs, realtime=True)
+        _check(reqs, exp, "idle")
+        assert reqs[0].count == 2 * (256 << 10) - 1
+        # the first 256 KiB request overflows its density-sized rows and is scanned again on the idle path;
+        # the 900 KiB one has more matches than the idle path holds and becomes a batch
+        assert st["rescans"] >= 1 and st["fast"] >= 3 and st["batches"] >= 1
+    finally:
+        srv.close()
