@@ -472,11 +472,13 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
     // reached by the first gram_len bytes, | GLOP_TERM when it is terminal;
     // without a start filter the initial state, encoded GLOP_TERM (state 0 is
     // never terminal).  0 when no pattern can start here.
-    auto probe = [&](const TextView &v, uint32_t off, uint32_t endr) -> uint32_t {
+    auto probe = [&](const TextView &v, uint32_t off, uint32_t endr, bool staged) -> uint32_t {
         if (FILT) {
             if (off + g > endr) return 0u;
             uint32_t w0 = 0, w1 = 0;
-            if (off + 12 <= v.n_stage) {
+            // (staged text: the 12 bytes from off < 1 KiB are inside the ring slot, and the gram's own
+            // bytes end at or before endr, so they were staged; bytes past them are masked off)
+            if (staged || off + 12 <= v.n_stage) {
                 const uint32_t *b32 = reinterpret_cast<const uint32_t *>(v.buf);
                 const uint32_t a = off >> 2, sh = 8 * (off & 3);
                 const uint32_t y1 = b32[a + 1];
@@ -747,7 +749,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
                         in = seg_of(qw, onchip, s0 + off, si, sstart, send);
                         endr = in ? (uint32_t)min(send - s0, (uint64_t)0xFFFFFFFFu) : 0u;
                     }
-                    if (in) val = probe(v, off, endr);
+                    if (in) val = probe(v, off, endr, !direct);
                 }
                 const uint32_t bm = __ballot_sync(FULL, val != 0);
                 __syncwarp();
@@ -914,11 +916,18 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
         // then does the producer arrive on the slot's full barrier again, so the
         // barrier is still in the copy's phase whenever the bit is set.)
         uint32_t issued = 0, par = 0;
+        // ring slot and round of step cs (cs % nstage, cs / nstage), kept without a division
+        uint32_t slot = 0, rnd = 0;
         for (uint32_t cs = 0;; ++cs) {
-            const uint32_t slot = cs % p.nstage;
-            if (cs >= p.nstage) {
+            if (cs) {
+                if (++slot == p.nstage) {
+                    slot = 0;
+                    ++rnd;
+                }
+            }
+            if (rnd) {
                 uint32_t ok = 1;
-                if (lane == 0) ok = mbar_wait(&mc->empty[slot], ((cs / p.nstage) - 1) & 1u, p.spin_budget) ? 1u : 0u;
+                if (lane == 0) ok = mbar_wait(&mc->empty[slot], (rnd - 1) & 1u, p.spin_budget) ? 1u : 0u;
                 ok = __shfl_sync(FULL, ok, 0);
                 if (!ok) {
                     if (lane == 0) atomicOr(p.hdr, WS_TIMEOUT);
@@ -966,7 +975,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
                 if (bulk && tma_ok) {
                     tma_load(dst, p.text + c0, bulk, &mc->full[slot]);
                     issued |= 1u << slot;
-                    par = (par & ~(1u << slot)) | (((cs / p.nstage) & 1u) << slot);
+                    par = (par & ~(1u << slot)) | ((rnd & 1u) << slot);
                 } else {
                     mbar_arrive(&mc->full[slot]);
                 }
@@ -982,9 +991,8 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
         __syncwarp();
     } else {
         const uint32_t cw = warp - 1;
-        for (uint32_t cs = 0;; ++cs) {
-            const uint32_t slot = cs % p.nstage;
-            if (!mbar_wait(&mc->full[slot], (cs / p.nstage) & 1u, p.spin_budget)) {
+        for (uint32_t slot = 0, ph = 0;;) {
+            if (!mbar_wait(&mc->full[slot], ph, p.spin_budget)) {
                 if (lane == 0) atomicOr(p.hdr, WS_TIMEOUT);
                 break;
             }
@@ -1009,6 +1017,10 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&mc->empty[slot]);
+            if (++slot == p.nstage) {
+                slot = 0;
+                ph ^= 1u;
+            }
         }
     }
 
