@@ -225,6 +225,8 @@ def make_workload(name: str):
         return W.config4()
     if name.startswith("syslog-") and name.endswith("MiB-1000pat"):
         return W.config2(int(name.split("-")[1][:-3]) * W.MiB)
+    if name.startswith("dpi-") and name.endswith("MiB-20000sig"):
+        return W.config3(int(name.split("-")[1][:-3]) * W.MiB)
     raise SystemExit("unknown workload " + name)
 
 
@@ -657,6 +659,8 @@ def main():
                     help="arrival seconds of the serving trace replayed for the default line's serve record")
     ap.add_argument("--dpi-steps", type=int, default=50)
     ap.add_argument("--serve-hbm-gib", type=int, default=16)
+    ap.add_argument("--smem-budget", type=int, default=0,
+                    help="shared-memory bytes for dense rows (0: automatic; 1: none, rows read through L1/L2)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_env()
@@ -697,7 +701,8 @@ def main():
     seg = None
     if w.seg is not None:
         seg = torch.from_numpy(w.seg.view(np.int64).copy()).to(dev)
-    a = glop.Automaton(w.patterns)
+    # (--smem-budget 1 keeps every dense row in L1/L2: the on-chip-table ablation)
+    a = glop.Automaton(w.patterns, smem_budget=args.smem_budget)
     stream = torch.cuda.Stream(device=dev)
     count = torch.zeros(1, dtype=torch.int64, device=dev)
     # size the output once (the count does not change between steps)
@@ -873,7 +878,9 @@ def main():
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": args.workload, "text_bytes": N, "text_sha256": text_sha, "patterns": w.patterns.n,
                    "matches": M,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": "dp%d (independent shards)" % ws},
+                   "l2": ("inputs larger than L2 (no flush)" if N > 129e6 else
+                          "inputs smaller than L2: a profiling case, not a bench number"),
+                   "parallelism": "dp%d (independent shards)" % ws},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None,
                      "note": "algorithmic bytes = text + halo re-reads + %d B/match + tile status; peak %s"
@@ -887,11 +894,13 @@ def main():
                     "p10": round(float(np.percentile(per, 10)), 5), "p90": round(float(np.percentile(per, 90)), 5),
                     "runs": len(per)},
     }
-    tr = profiled_traffic(args.workload)
+    if args.smem_budget:
+        line["config"]["smem_budget_bytes"] = args.smem_budget
+    tr = profiled_traffic(args.workload) if not args.smem_budget else None
     if tr is not None:
         line["roofline"]["traffic"] = tr
     # the limit that binds: instruction issue (4 schedulers per SM, one warp instruction per cycle each)
-    ins = profiled_value(args.workload, "issue", "inst_per_launch")
+    ins = profiled_value(args.workload, "issue", "inst_per_launch") if not args.smem_budget else None
     f_sm = (clk or {}).get("sm_mhz") or 2070.0
     if ins is not None:
         peak_issue = 4 * SMS * f_sm * 1e6

@@ -251,8 +251,7 @@ int compile_host(const uint8_t *bytes, const uint64_t *offs, uint32_t n, uint32_
             uint32_t w0 = (uint32_t)gb[0] | ((uint32_t)gb[1] << 8) | ((uint32_t)gb[2] << 16) | ((uint32_t)gb[3] << 24);
             uint32_t w1 = ((uint32_t)gb[4] | ((uint32_t)gb[5] << 8) | ((uint32_t)gb[6] << 16) | ((uint32_t)gb[7] << 24)) & mask1;
             uint32_t h = glop_gram_hash(w0, w1);
-            uint32_t bi = glop_bitmap_index(h, A.bm_log2);
-            A.bitmap[bi >> 5] |= 0x80000000u >> (bi & 31);  // bit order reversed within a word
+            A.bitmap[glop_bitmap_word(h, A.bm_log2)] |= 0x80000000u >> glop_bitmap_bit(h, w0, g, A.bm_log2);
             uint32_t slot = glop_table_slot(h, A.ht_log2), m = (1u << A.ht_log2) - 1;
             while (A.grams[slot].val) slot = (slot + 1) & m;
             A.grams[slot] = GlopGramSlot{w0, w1, enc(v), 0};

@@ -65,6 +65,6 @@ struct GlopDevAutomaton {
     const uint32_t *outl;          // [2 * n_states] the same lists as (start, count) pairs, one 8-byte load each
     const uint32_t *cum_ids;       // pattern ids, ascending within a list
     uint32_t n_cum_ids;            // entries of cum_ids
-    const uint32_t *bitmap;        // [(1 << bm_log2) / 32]; index i is bit (31 - i % 32) of word i / 32
+    const uint32_t *bitmap;        // [(1 << bm_log2) / 32]; a gram's word and bit as glop_hash.h places them
     const GlopGramSlot *grams;     // [1 << ht_log2]
 };

@@ -122,9 +122,9 @@ int glop_hostcheck_scan_iters(const uint8_t *pat, const uint64_t *poff, uint32_t
                 uint32_t w0 = rd32(text + i, hi - i);
                 uint32_t w1 = rd32(text + i + 4, hi - i - 4) & glop_w1_mask(g);
                 uint32_t h = glop_gram_hash(w0, w1);
-                uint32_t bi = glop_bitmap_index(h, A.bm_log2);
+                const uint32_t bw = glop_bitmap_word(h, A.bm_log2), bb = glop_bitmap_bit(h, w0, g, A.bm_log2);
                 if (iters) iters[i] = 255;
-                if (!((A.bitmap[bi >> 5] << (bi & 31)) & 0x80000000u)) continue;
+                if (!((A.bitmap[bw] << bb) & 0x80000000u)) continue;
                 if (iters) iters[i] = 0;
                 ++passed;
                 uint32_t m = (1u << A.ht_log2) - 1, slot = glop_table_slot(h, A.ht_log2), v = 0;

@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
 
     const uint32_t g = A.gram_len;
     const uint32_t w1mask = FILT == 8 ? glop_w1_mask(g) : 0u;
-    const uint32_t bsh = 32u - A.bm_log2;
+    const uint32_t wsh = 37u - A.bm_log2, bsh = 32u - A.bm_log2;  // a gram's bitmap word and (longer grams) bit
     const uint32_t htmask = (1u << A.ht_log2) - 1u;
     // Scratch record of a matching offset.  Single buffer: (t << 10) | offset in
     // its sub-tile, t the deepest terminal state (below 2^22: larger automata
@@ -540,12 +540,19 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
         for (int j = 31; j >= 0; --j) {
             uint32_t rot;
             if (FILT) {
-                uint32_t h = __funnelshift_r(x[j >> 2], x[(j >> 2) + 1], 8 * (j & 3)) * GLOP_HASH_M0;
-                if (FILT == 8)
-                    h ^= (__funnelshift_r(x[(j >> 2) + 1], x[(j >> 2) + 2], 8 * (j & 3)) & w1mask) * GLOP_HASH_M1;
-                const uint32_t bi = h >> bsh;
-                const uint32_t word = bm_s[bi >> 5];
-                rot = __funnelshift_l(word, word, bi);
+                const uint32_t w0 = __funnelshift_r(x[j >> 2], x[(j >> 2) + 1], 8 * (j & 3));
+                if (FILT == 4) {
+                    // one wide multiply: the low half picks the word, the high half's low 5 bits the bit
+                    const unsigned long long pr = (unsigned long long)w0 * GLOP_HASH_M0;
+                    const uint32_t word = bm_s[(uint32_t)pr >> wsh];
+                    rot = __funnelshift_l(word, word, (uint32_t)(pr >> 32));
+                } else {
+                    const uint32_t h =
+                        w0 * GLOP_HASH_M0 ^
+                        (__funnelshift_r(x[(j >> 2) + 1], x[(j >> 2) + 2], 8 * (j & 3)) & w1mask) * GLOP_HASH_M1;
+                    const uint32_t word = bm_s[h >> wsh];
+                    rot = __funnelshift_l(word, word, h >> bsh);
+                }
             } else {
                 const uint32_t by = (x[j >> 2] >> (8 * (j & 3))) & 0xFFu;
                 rot = fb_s[by >> 5] << (31 - (by & 31));
