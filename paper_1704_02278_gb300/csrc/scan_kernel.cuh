@@ -615,7 +615,9 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
         // slot i is the number of lanes that start at or before i, less one: the lanes that started in
         // earlier rounds plus the starts at or below this lane's slot in a mask of this round's starts.
         const uint32_t nz = __ballot_sync(FULL, c != 0u);
-        const bool prefix = (nz & (nz + 1u)) == 0u;
+        // (long lists -- 8 or more outputs a record on average -- keep the shuffle search: most rounds then
+        // belong to one or two records, and a warp reduction every round costs more than it saves)
+        const bool prefix = (nz & (nz + 1u)) == 0u && tot < 8u * __popc(nz);
         const uint32_t le = (2u << lane) - 1u;
         const uint32_t room = o < p.cap ? (uint32_t)min(p.cap - o, (unsigned long long)tot) : 0u;
         uint32_t before = 0;

@@ -247,3 +247,20 @@ def test_scan_host_pieces_cross_boundaries_and_overflow():
     assert total2 == len(exp)
     assert np.array_equal(got2, exp[:cap])
     a.close()
+
+
+def test_output_lists_past_2_22_entries():
+    """More than 2^22 output-list entries in all (here 2^22 + 9 copies of one pattern): a sub-tile's match count
+    is summed in 64 bits (the 32-bit sums hold only below that), and one offset expands into millions of rows."""
+    n_dup = (1 << 22) + 9
+    buf = np.frombuffer(b"ab" * n_dup + b"b", np.uint8).copy()
+    offs = np.concatenate([np.arange(0, 2 * n_dup + 1, 2, dtype=np.uint64), np.array([2 * n_dup + 1], np.uint64)])
+    pats = W.Patterns(buf, offs)
+    text = np.full(3000, ord("x"), np.uint8)
+    for i in (0, 7, 2000):  # two "ab" in sub-tile 0, one in sub-tile 1
+        text[i:i + 2] = np.frombuffer(b"ab", np.uint8)
+    exp = oracle.ac(text, pats.csr())
+    assert len(exp) == 3 * (n_dup + 1)
+    got, n = gpu_scan(pats, text, capacity=len(exp))
+    assert n == len(exp)
+    assert np.array_equal(got, exp)
