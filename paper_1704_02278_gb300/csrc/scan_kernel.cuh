@@ -783,19 +783,21 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
                 uint32_t nxt = 0, qi = 0, st = 0, pos = 0, t = 0, endw = endsub;
                 bool have = false;
                 while (true) {
-                    const uint32_t wm = __ballot_sync(FULL, !have);
-                    if (!have) {
-                        const uint32_t k = nxt + __popc(wm & lt);
-                        if (k < ncont) {
-                            qi = cidx[k];
-                            st = cst[k];
-                            pos = cpos[k];
-                            t = qst[qi];
-                            if (BATCH) endw = qend[qi];
-                            have = true;
+                    if (nxt < ncont) {  // (once every listed walk is handed out, lanes only finish theirs)
+                        const uint32_t wm = __ballot_sync(FULL, !have);
+                        if (!have) {
+                            const uint32_t k = nxt + __popc(wm & lt);
+                            if (k < ncont) {
+                                qi = cidx[k];
+                                st = cst[k];
+                                pos = cpos[k];
+                                t = qst[qi];
+                                if (BATCH) endw = qend[qi];
+                                have = true;
+                            }
                         }
+                        nxt += __popc(wm);
                     }
-                    nxt += __popc(wm);
                     if (!__any_sync(FULL, have)) break;
                     // the direct (re-walk) mode reads the text from global memory: no staged bytes
                     const bool fin = have && (direct ? step<ROW16, true>(A, cls_s, rows_s, hot_n, v, st, pos, endw, t, p.hdr)
