@@ -616,11 +616,16 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
         // earlier rounds plus the starts at or below this lane's slot in a mask of this round's starts.
         const uint32_t nz = __ballot_sync(FULL, c != 0u);
         // (long lists -- 8 or more outputs a record on average -- keep the shuffle search: most rounds then
-        // belong to one or two records, and a warp reduction every round costs more than it saves)
-        const bool prefix = (nz & (nz + 1u)) == 0u && tot < 8u * __popc(nz);
+        // belong to one or two records, and a warp reduction every round costs more than it saves.  In batch
+        // mode, a round that one record owns entirely needs no search at all: the owner of each round's first
+        // slot is carried from round to round.  The single-buffer kernel keeps the plain search, where that
+        // bookkeeping measured slower.)
+        const bool pre = (nz & (nz + 1u)) == 0u;
+        const bool prefix = pre && tot < 8u * __popc(nz), track = BATCH && pre && !prefix;
         const uint32_t le = (2u << lane) - 1u;
         const uint32_t room = o < p.cap ? (uint32_t)min(p.cap - o, (unsigned long long)tot) : 0u;
         uint32_t before = 0;
+        uint32_t cur = 0, cur_end = track ? __shfl_sync(FULL, incl, 0) : 0u;  // owner of slot s0, end of its slots
         for (uint32_t s0 = 0; s0 < tot; s0 += 32) {
             const uint32_t slot = s0 + lane;
             uint32_t ow;
@@ -628,8 +633,21 @@ __global__ void __launch_bounds__(THREADS, 1) scan_kernel(const __grid_constant_
                 const uint32_t starts = __reduce_or_sync(FULL, (c && excl - s0 < 32u) ? 1u << (excl - s0) : 0u);
                 ow = before + __popc(starts & le) - 1u;
                 before += __popc(starts);
+            } else if (track && cur_end >= s0 + 32u) {
+                ow = cur;
             } else {
                 ow = owner_of(excl, slot);
+            }
+            if (track) {
+                // the owner of slot s0 + 32: the last slot's, or the next lane when that one ends here
+                if (cur_end < s0 + 32u) {
+                    cur = __shfl_sync(FULL, ow, 31);
+                    cur_end = __shfl_sync(FULL, incl, cur);
+                }
+                if (cur_end == s0 + 32u && cur < 31u) {
+                    ++cur;
+                    cur_end = __shfl_sync(FULL, incl, cur);
+                }
             }
             const uint32_t base_o = __shfl_sync(FULL, base, ow), f0_o = __shfl_sync(FULL, f0, ow);
             const uint32_t f1_o = BATCH ? __shfl_sync(FULL, f1, ow) : 0u;
