@@ -809,8 +809,8 @@ glop_status glop_server_poll(glop_server S, glop_server_result *res, uint32_t ma
         }
         if (*n_res || now_ns() >= t_end) break;
         if (S->inflight.empty() && S->pending.empty() && !S->lane_active) break;
-        // Waiting: a tight loop of event queries contends with the lane's thread for the driver (its copies
-        // and launches are many short calls), so after a few idle turns the loop sleeps between queries.
+        // Waiting: after a few idle turns the loop sleeps between rounds of event queries instead of spinning
+        // on them, leaving the core (and the driver) to the lane's thread and the caller.
         if (S->inflight.size() != n_inflight || S->pending.size() != n_pending) idle = 0;
         if (++idle > 16) std::this_thread::sleep_for(std::chrono::microseconds(10));
         else std::this_thread::yield();
